@@ -1,0 +1,170 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) staggered-fermion library.
+ *
+ * The library computes, on one GPU, the SU(3) link arithmetic that arXiv:1309.0551
+ * ("Optimizing the performance of Lattice Gauge Theory simulations with Streaming SIMD
+ * extensions") identifies as the bulk of a staggered lattice code's run time (Sec. 4:
+ * the routines of Table 1 take 80-90% of it), in the form where it dominates: the
+ * even/odd staggered Dslash and the conjugate-gradient solve it drives, plus the fermion
+ * force.  Everything crossing this boundary is a plain pointer, size or enum.
+ *
+ * ---------------------------------------------------------------------------------------
+ * Conventions (the paper states none of them; these are the library's):
+ *   dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2, periodic.  V = Lx*Ly*Lz*Lt,
+ *   Vh = V/2.  lex = x + Lx*(y + Ly*(z + Lz*t)); parity = (x+y+z+t) & 1, even = 0;
+ *   checkerboard index cb = lex >> 1 (the sites of one parity in lex order).
+ *   Staggered phases eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z).
+ *
+ *   Gauge field, canonical:  complex128 U[4][V][3][3]  (U[mu][lex][row][col], the link
+ *   from x to x+mu; interleaved re,im doubles; 16-byte aligned).
+ *   Colour-vector field on one parity, canonical:  complex T v[nrhs][Vh][3] with T the
+ *   vector precision (interleaved re,im; f64 = 2 doubles, f32 = 2 floats, bf16/f16 = 2
+ *   16-bit values); 16-byte aligned base.
+ *   SU(3) matrices for the batched routines: complex T A[n][3][3], row-major.
+ *
+ *   (D chi)(x) = sum_mu eta_mu(x) [ U_mu(x) chi(x+mu) - U_mu(x-mu)^dag chi(x-mu) ]
+ *   (no factor 1/2).  M = m^2 - D_eo D_oe on even sites (Hermitian positive definite).
+ *
+ * Memory: every pointer argument named "device" is a device pointer on the context's
+ * device, owned by the caller and only read or written during the call's stream work.
+ * lq_gauge objects and the context's scratch space are owned by the library.  Every call
+ * is asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ * stream) unless it says it synchronises.
+ *
+ * Errors: every entry point returns an lq_status; nothing aborts or traps.  On failure
+ * lq_last_error(ctx) gives a message.  LQ_ERR_INVALID_ARG covers NULL pointers, odd or
+ * non-positive extents, pointers not 16-byte aligned, unsupported precision pairs and
+ * nrhs outside [1, 16].  A CUDA error is reported as LQ_ERR_CUDA with CUDA's string.
+ * ---------------------------------------------------------------------------------------
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQ_OK = 0,
+  LQ_ERR_INVALID_ARG = 1,
+  LQ_ERR_CUDA = 2,
+  LQ_ERR_NOT_CONVERGED = 3,
+  LQ_ERR_NUMERIC = 4,       /* NaN/Inf met (e.g. in a CG source or residual) */
+  LQ_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  LQ_ERR_UNSUPPORTED = 6
+} lq_status;
+
+typedef enum { LQ_F64 = 0, LQ_F32 = 1, LQ_BF16 = 2, LQ_F16 = 3 } lq_prec;
+typedef enum { LQ_RECON_18 = 18, LQ_RECON_12 = 12 } lq_recon;
+
+typedef void* lq_stream;                 /* a cudaStream_t */
+typedef struct lq_context lq_context;    /* device, scratch space, tuning cache, last error */
+typedef struct lq_gauge lq_gauge;        /* packed links, library-owned device copy */
+
+/* ----------------------------------------------------------------- context ---------- */
+
+/* Create a context on CUDA device `device`.  *ctx receives the handle. */
+lq_status lq_create(lq_context** ctx, int device);
+/* Free a context and its scratch space (synchronises the device).  NULL is a no-op. */
+lq_status lq_destroy(lq_context* ctx);
+/* Message of the last failing call on this context ("" if none).  Valid until the next
+ * call on the same context. */
+const char* lq_last_error(const lq_context* ctx);
+/* Name of a status code. */
+const char* lq_status_string(lq_status s);
+/* Autotuning of launch shapes (block size, right-hand sides per thread): 1 = on (the
+ * default, unless the environment sets LQCD_TUNE=0), 0 = fixed defaults.  Tuning times
+ * candidate launches on the first call with a new shape key and must not happen during
+ * stream capture; call lq_tune_warmup-style entry points first when capturing. */
+lq_status lq_set_tuning(lq_context* ctx, int enable);
+/* Write the tuning table (one line per key: key, chosen block, rhs tile, microseconds)
+ * into buf (NUL-terminated, truncated to len).  *needed receives the full length + 1. */
+lq_status lq_tune_report(const lq_context* ctx, char* buf, size_t len, size_t* needed);
+
+/* ------------------------------------------------------------------- gauge ---------- */
+
+/* Pack a canonical complex128 gauge field (device, U[4][V][3][3]) into the library's
+ * internal layout with storage precision `prec` and `recon` reals per link.
+ *   Internal layout: structure of arrays per (direction, parity) block, sites in
+ *   checkerboard order, the reals of a link split into "planes" of 16-byte (or smaller)
+ *   chunks so that each thread reads its link with few wide coalesced loads.  Recon 12
+ *   keeps rows 0 and 1; row 2 is rebuilt as conj(row0 x row1) in registers (exact for
+ *   SU(3) links up to rounding).  Reduced precisions round each real once (to nearest,
+ *   ties to even) from FP64.
+ * The gauge object keeps no reference to U. */
+lq_status lq_gauge_pack(lq_context* ctx, const int dims[4], const void* U_canon,
+                        lq_prec prec, lq_recon recon, lq_gauge** out, lq_stream stream);
+lq_status lq_gauge_free(lq_context* ctx, lq_gauge* g);
+/* Bytes of device memory the packed field occupies (for bandwidth accounting). */
+lq_status lq_gauge_info(const lq_gauge* g, int dims[4], lq_prec* prec, lq_recon* recon,
+                        size_t* bytes);
+
+/* -------------------------------------------------------- SU(3) batches ------------- */
+
+/* C[i] = op(A[i]) op(B[i]) for i < n; op = adjoint when adjA / adjB is 1.  Table 1:
+ * mult_su3_nn (0,0), mult_su3_an (1,0), mult_su3_na (0,1).  198 flops per product.
+ * A, B, C: device, complex [n][3][3] of `prec` (LQ_F64 or LQ_F32); C must not overlap
+ * A or B.  n = 0 is a no-op. */
+lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, int64_t n,
+                        int adjA, int adjB, lq_prec prec, lq_stream stream);
+
+/* c[i] = op(A[i]) b[i]; op = adjoint when adj = 1.  Table 1: mult_su3_mat_vec (adj 0) and
+ * mult_adj_su3_mat_vec (adj 1; its first component is Eqs. (1.1)-(2.3)).  66 flops each.
+ * A: device complex [n][3][3]; b, c: device complex [n][3]; prec LQ_F64 or LQ_F32. */
+lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* c,
+                           int64_t n, int adj, lq_prec prec, lq_stream stream);
+
+/* ------------------------------------------------------------------ Dslash ---------- */
+
+/* Half Dslash: out = D in restricted to the sites of parity `out_parity`, `in` living on
+ * the other parity (out_parity 1: D_oe, 0: D_eo), for nrhs right-hand sides that share
+ * each loaded link.  570 flops per output site and right-hand side.
+ *   in, out: device, canonical vector fields [nrhs][Vh][3] of `vec_prec`; must not overlap.
+ *   Precision pairs: an LQ_F64 gauge needs LQ_F64 vectors (FP64 arithmetic); an LQ_F32,
+ *   LQ_BF16 or LQ_F16 gauge takes LQ_F32, LQ_BF16 or LQ_F16 vectors (FP32 arithmetic and
+ *   accumulation, one rounding at the store).  16-bit vectors carry no scale factor: their
+ *   values must lie in the format's range.
+ *   nrhs in [1, 16]. */
+lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
+                    int out_parity, int nrhs, lq_prec vec_prec, lq_stream stream);
+
+/* ---------------------------------------------------------------------- CG ---------- */
+
+typedef struct {
+  double tol;          /* stop when ||b - M x|| / ||b|| <= tol, M in FP64 (true residual) */
+  int maxiter;         /* inner iterations, all right-hand sides together */
+  int reliable_every;  /* mixed precision: FP64 residual replacement at least this often */
+  double delta;        /* mixed precision: ... or when ||r_lo|| < delta * ||r|| at the last one */
+  int check_every;     /* iterations per device-resident block between host checks (graph) */
+} lq_cg_params;
+
+typedef struct {
+  int iters;              /* inner iterations until this right-hand side converged */
+  int reliable_updates;   /* FP64 residual replacements (mixed precision) */
+  double true_rel_resid;  /* ||b - M x|| / ||b|| recomputed in FP64 at exit */
+  double seconds;         /* wall time of the whole call */
+} lq_cg_stats;
+
+/* Solve M x = b, M = m^2 - D_eo D_oe on even sites, by conjugate gradient from x = 0.
+ *   U_hi: LQ_F64 gauge (recon 18 or 12): defines M and every true residual.
+ *   U_lo: NULL -> plain FP64 CG.  Otherwise an LQ_F32 / LQ_BF16 / LQ_F16 gauge of the same
+ *         lattice: the inner iteration applies M with those links, keeps its vectors in
+ *         FP32 with FP64 inner products, and replaces its residual by the FP64 true
+ *         residual (reliable update) every params->reliable_every iterations, or when it
+ *         fell below params->delta times the last replaced one, or on apparent convergence.
+ *   b, x: device complex128 [nrhs][Vh][3]; x is overwritten.  nrhs in [1, 16].
+ *   stats: host array of nrhs entries (may be NULL).
+ * Synchronises `stream` at each check (every check_every iterations).  Returns
+ * LQ_ERR_NOT_CONVERGED if maxiter was reached (stats filled in), LQ_ERR_NUMERIC if b or a
+ * residual holds NaN/Inf. */
+lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, double mass,
+                   const void* b, void* x, int nrhs, const lq_cg_params* params,
+                   lq_cg_stats* stats, lq_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

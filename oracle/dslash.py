@@ -103,3 +103,27 @@ def dense_normal(U, mass, dims):
     Doe = dense_block(D, dims, 1)
     Deo = dense_block(D, dims, 0)
     return mass * mass * np.eye(Doe.shape[1]) - Deo @ Doe
+
+
+def dslash_eo_sites(U, chi_cb, dims, out_parity, cb_sites):
+    """``dslash_eo`` evaluated only at the checkerboard sites ``cb_sites`` of parity
+    ``out_parity`` (for sampled checks on lattices too large for the full oracle).  Plain
+    loops with integer neighbour arithmetic; ``chi_cb`` is (Vh, 3) on the other parity."""
+    dims = tuple(dims)
+    V = int(np.prod(dims))
+    U = np.asarray(U).reshape(4, V, 3, 3)
+    par = geo.parity(dims).reshape(-1)
+    lex_of = {p: np.flatnonzero(par == p) for p in (0, 1)}
+    out = np.zeros((len(cb_sites), 3), dtype=np.complex128)
+    for n, cb in enumerate(cb_sites):
+        x = int(lex_of[out_parity][cb])
+        cx = geo.site_coords(dims, x)
+        phases = (1, (-1) ** cx[0], (-1) ** (cx[0] + cx[1]), (-1) ** (cx[0] + cx[1] + cx[2]))
+        acc = np.zeros(3, dtype=np.complex128)
+        for mu in range(4):
+            yf = geo.neighbour_lex(dims, x, mu, +1)
+            yb = geo.neighbour_lex(dims, x, mu, -1)
+            acc += phases[mu] * mult_su3_mat_vec(U[mu, x], chi_cb[yf >> 1])
+            acc -= phases[mu] * mult_adj_su3_mat_vec(U[mu, yb], chi_cb[yb >> 1])
+        out[n] = acc
+    return out

@@ -1,0 +1,219 @@
+"""Python binding of ``liblqcd.so``, the GB300 staggered Dslash / CG / force library.
+
+Argument marshalling only: every function here forwards to the C entry point of the same
+name (``include/lqcd.h``) with tensor data pointers and the current CUDA stream; all
+arithmetic runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.  The binding never falls back to another implementation: if the library is not
+built, or a call fails, it raises.
+
+Vector and matrix tensors use the canonical layouts of ``lqcd.h``: complex128 / complex64
+tensors for FP64 / FP32, and real tensors with a trailing (re, im) axis of dtype bfloat16
+or float16 for the 16-bit formats.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB, build as _build  # noqa: F401
+
+LQ_F64, LQ_F32, LQ_BF16, LQ_F16 = 0, 1, 2, 3
+PREC = {"f64": LQ_F64, "f32": LQ_F32, "bf16": LQ_BF16, "f16": LQ_F16}
+PREC_NAME = {v: k for k, v in PREC.items()}
+LQ_RECON_18, LQ_RECON_12 = 18, 12
+
+_lib = None
+
+
+class LQError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status}: {msg}")
+        self.status = status
+
+
+class lq_cg_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int),
+                ("reliable_every", ctypes.c_int), ("delta", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class lq_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load(path: str | None = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1309_0551_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    sigs = {
+        "lq_create": ([ctypes.POINTER(P), I], I),
+        "lq_destroy": ([P], I),
+        "lq_last_error": ([P], ctypes.c_char_p),
+        "lq_status_string": ([I], ctypes.c_char_p),
+        "lq_set_tuning": ([P, I], I),
+        "lq_tune_report": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
+        "lq_gauge_pack": ([P, ctypes.POINTER(I), P, I, I, ctypes.POINTER(P), P], I),
+        "lq_gauge_free": ([P, P], I),
+        "lq_gauge_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                           ctypes.POINTER(ctypes.c_size_t)], I),
+        "su3_mul_batch": ([P, P, P, P, L, I, I, I, P], I),
+        "su3_matvec_batch": ([P, P, P, P, L, I, I, P], I),
+        "dslash_eo": ([P, P, P, P, I, I, I, P], I),
+        "cg_solve": ([P, P, P, D, P, P, I, ctypes.POINTER(lq_cg_params),
+                      ctypes.POINTER(lq_cg_stats), P], I),
+    }
+    for name, (args, res) in sigs.items():
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Context:
+    """An ``lq_context``: device, scratch space, tuning table, last error."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.lq_create(ctypes.byref(h), int(device))
+        if st != 0:
+            raise LQError(self.lib.lq_status_string(st).decode(), f"lq_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+
+    def check(self, st):
+        if st != 0:
+            raise LQError(self.lib.lq_status_string(st).decode(),
+                          self.lib.lq_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            self.lib.lq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, enable: bool):
+        self.check(self.lib.lq_set_tuning(self.handle, int(bool(enable))))
+
+    def tune_report(self) -> str:
+        need = ctypes.c_size_t()
+        self.check(self.lib.lq_tune_report(self.handle, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        self.check(self.lib.lq_tune_report(self.handle, buf, need.value, None))
+        return buf.value.decode()
+
+
+class Gauge:
+    """A packed gauge field (``lq_gauge``), freed with the object."""
+
+    def __init__(self, ctx: Context, handle, dims, prec, recon):
+        self.ctx, self.handle, self.dims, self.prec, self.recon = ctx, handle, tuple(dims), prec, recon
+
+    @property
+    def nbytes(self) -> int:
+        n = ctypes.c_size_t()
+        self.ctx.check(self.ctx.lib.lq_gauge_info(self.handle, None, None, None, ctypes.byref(n)))
+        return n.value
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.lq_gauge_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vec_prec_of(t) -> int:
+    import torch
+    return {torch.complex128: LQ_F64, torch.complex64: LQ_F32,
+            torch.bfloat16: LQ_BF16, torch.float16: LQ_F16}[t.dtype]
+
+
+def lq_gauge_pack(ctx: Context, dims, U, prec, recon=18, stream=None) -> Gauge:
+    """Pack a canonical complex128 gauge field (4, V, 3, 3) on the device."""
+    import torch
+    if U.dtype != torch.complex128 or not U.is_cuda or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex128 CUDA tensor of shape (4, V, 3, 3)")
+    prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    h = ctypes.c_void_p()
+    ctx.check(ctx.lib.lq_gauge_pack(ctx.handle, d, _ptr(U), prec, int(recon), ctypes.byref(h),
+                                    _stream(stream)))
+    return Gauge(ctx, h, dims, prec, int(recon))
+
+
+def dslash_eo(ctx: Context, U: Gauge, inp, out, out_parity: int, nrhs: int = 1, vec_prec=None,
+              stream=None):
+    """out = D inp on parity ``out_parity`` (canonical [nrhs][Vh][3] vectors)."""
+    vp = vec_prec_of(inp) if vec_prec is None else vec_prec
+    ctx.check(ctx.lib.dslash_eo(ctx.handle, U.handle, _ptr(inp), _ptr(out), int(out_parity),
+                                int(nrhs), int(vp), _stream(stream)))
+
+
+def su3_mul_batch(ctx: Context, A, B, C, n=None, adjA=0, adjB=0, prec=None, stream=None):
+    """C[i] = op(A[i]) op(B[i]) (Table 1: mult_su3_nn / _an / _na)."""
+    n = A.shape[0] if n is None else n
+    prec = vec_prec_of(A) if prec is None else prec
+    ctx.check(ctx.lib.su3_mul_batch(ctx.handle, _ptr(A), _ptr(B), _ptr(C), int(n), int(adjA),
+                                    int(adjB), int(prec), _stream(stream)))
+
+
+def su3_matvec_batch(ctx: Context, A, b, c, n=None, adj=0, prec=None, stream=None):
+    """c[i] = op(A[i]) b[i] (Table 1: mult_su3_mat_vec / mult_adj_su3_mat_vec)."""
+    n = A.shape[0] if n is None else n
+    prec = vec_prec_of(A) if prec is None else prec
+    ctx.check(ctx.lib.su3_matvec_batch(ctx.handle, _ptr(A), _ptr(b), _ptr(c), int(n), int(adj),
+                                       int(prec), _stream(stream)))
+
+
+def cg_solve(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float, b, x, nrhs: int = 1,
+             tol=1e-10, maxiter=10000, reliable_every=100, delta=0.1, check_every=20, stream=None):
+    """Solve (m^2 - D_eo D_oe) x = b on even sites; returns a list of per-rhs stats dicts.
+    Raises LQError on failure (including LQ_ERR_NOT_CONVERGED)."""
+    params = lq_cg_params(float(tol), int(maxiter), int(reliable_every), float(delta), int(check_every))
+    stats = (lq_cg_stats * int(nrhs))()
+    st = ctx.lib.cg_solve(ctx.handle, U_hi.handle, None if U_lo is None else U_lo.handle,
+                          float(mass), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(params),
+                          stats, _stream(stream))
+    out = [dict(iters=s.iters, reliable_updates=s.reliable_updates,
+                true_rel_resid=s.true_rel_resid, seconds=s.seconds) for s in stats]
+    if st != 0:
+        err = LQError(ctx.lib.lq_status_string(st).decode(), ctx.lib.lq_last_error(ctx.handle).decode())
+        err.stats = out
+        raise err
+    return out

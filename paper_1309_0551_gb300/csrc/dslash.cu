@@ -1,0 +1,142 @@
+// dslash_eo entry point and the internal launcher (tuned launch shape) used by the solvers.
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "dslash_kernel.cuh"
+
+static const char* prec_name(lq_prec p) {
+  switch (p) {
+    case LQ_F64: return "f64";
+    case LQ_F32: return "f32";
+    case LQ_BF16: return "bf16";
+    case LQ_F16: return "f16";
+  }
+  return "?";
+}
+
+static DslashLaunchFn pick_fn(const lq_gauge* g) {
+  switch (g->prec) {
+    case LQ_F64: return dslash_fn_f64(g->recon);
+    case LQ_F32: return dslash_fn_f32(g->recon);
+    case LQ_BF16: return dslash_fn_bf16(g->recon);
+    case LQ_F16: return dslash_fn_f16(g->recon);
+  }
+  return nullptr;
+}
+
+bool dslash_vec_ok(lq_prec gauge, lq_prec vec) {
+  if (gauge == LQ_F64) return vec == LQ_F64;
+  return vec == LQ_F32 || vec == LQ_BF16 || vec == LQ_F16;
+}
+
+static std::string dslash_key(const lq_gauge* g, lq_prec vp, int nrhs) {
+  char buf[160];
+  snprintf(buf, sizeof buf, "dslash g=%s/%d v=%s dims=%dx%dx%dx%d nrhs=%d", prec_name(g->prec),
+           (int)g->recon, prec_name(vp), g->dims[0], g->dims[1], g->dims[2], g->dims[3], nrhs);
+  return buf;
+}
+
+// Candidate launch shapes, default first.  FP64 tiles stop at 4 right-hand sides (eight
+// FP64 accumulators per rhs already cost 12 registers each).
+static std::vector<TuneEntry> dslash_candidates(lq_prec gp, int nrhs) {
+  std::vector<int> tiles;
+  for (int t : {1, 2, 4, 8})
+    if (t <= nrhs && !(gp == LQ_F64 && t > 4)) tiles.push_back(t);
+  int first_tile = 1;
+  for (int t : tiles)
+    if (t <= (gp == LQ_F64 ? 2 : 4)) first_tile = t;
+  std::vector<TuneEntry> c;
+  c.push_back(TuneEntry{128, first_tile, 0.f});
+  for (int t : tiles)
+    for (int b : {64, 128, 256})
+      if (!(b == 128 && t == first_tile)) c.push_back(TuneEntry{b, t, 0.f});
+  return c;
+}
+
+// Smallest block size any candidate uses (bounds the reduction partials per rhs).
+int dslash_min_block() { return 64; }
+
+static DslashKArgs make_kargs(const DslashArgs& a) {
+  DslashKArgs k;
+  k.gauge = a.U->data;
+  k.blk_bytes = a.U->blk_bytes;
+  k.G = make_geom(a.U);
+  k.out_par = a.out_parity;
+  k.in = a.in;
+  k.out = a.out;
+  k.rhs_stride = a.rhs_stride ? a.rhs_stride : (size_t)a.U->Vh;
+  k.nrhs = a.nrhs;
+  k.w1 = a.w1; k.a1 = a.a1;
+  k.w2 = a.w2; k.a2 = a.a2;
+  k.c = a.c;
+  k.reduce = a.reduce;
+  if (a.red) k.red = *a.red;
+  else k.red = Reducer{nullptr, nullptr, nullptr, 0, 0, nullptr};
+  return k;
+}
+
+lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
+  DslashLaunchFn fn = pick_fn(a.U);
+  if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
+  DslashKArgs k = make_kargs(a);
+  // Tune on the plain operator (no epilogue, no reduction: repeatable launches), then use
+  // the chosen shape for this launch.
+  DslashKArgs plain = k;
+  plain.w1 = plain.w2 = nullptr;
+  plain.a1 = plain.a2 = 0.0;
+  plain.c = 1.0;
+  plain.reduce = RED_NONE;
+  TuneEntry pick;
+  lq_status st = tune_pick(
+      ctx, dslash_key(a.U, a.vec_prec, a.nrhs), dslash_candidates(a.U->prec, a.nrhs), s,
+      [&](const TuneEntry& c) -> lq_status {
+        cudaError_t e = fn(plain, a.vec_prec, c.block, c.rhs_tile, s);
+        if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash (tuning)");
+        return LQ_OK;
+      },
+      &pick);
+  if (st) return st;
+  if (a.reduce != RED_NONE) {
+    int nbx = (k.G.Vh + pick.block - 1) / pick.block;
+    if (!a.red || nbx > a.red->nblocks_max)
+      return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
+  }
+  cudaError_t e = fn(k, a.vec_prec, pick.block, pick.rhs_tile, s);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash");
+  return LQ_OK;
+}
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+extern "C" lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
+                               int out_parity, int nrhs, lq_prec vec_prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (!U) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "gauge is NULL");
+  if (!in || !out) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "in/out is NULL");
+  if (!lq_aligned16(in) || !lq_aligned16(out))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+  if (out_parity != 0 && out_parity != 1)
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "out_parity must be 0 or 1");
+  if (nrhs < 1 || nrhs > 16) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  if (vec_prec < LQ_F64 || vec_prec > LQ_F16 || !dslash_vec_ok(U->prec, vec_prec))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "vector precision %d does not pair with gauge precision %d",
+                   (int)vec_prec, (int)U->prec);
+  size_t vbytes = (size_t)nrhs * U->Vh * 6 * lq_prec_bytes(vec_prec);
+  if (overlap(in, vbytes, out, vbytes)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "in and out overlap");
+  DeviceGuard dg(ctx->device);
+  DslashArgs a;
+  a.U = U;
+  a.in = in;
+  a.out = out;
+  a.out_parity = out_parity;
+  a.nrhs = nrhs;
+  a.vec_prec = vec_prec;
+  a.rhs_stride = U->Vh;
+  return launch_dslash(ctx, a, (cudaStream_t)stream);
+}

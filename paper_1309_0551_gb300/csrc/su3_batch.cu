@@ -1,0 +1,175 @@
+// Batched SU(3) products of Table 1: mult_su3_nn / mult_su3_an / mult_su3_na
+// (su3_mul_batch) and mult_su3_mat_vec / mult_adj_su3_mat_vec (su3_matvec_batch).
+//
+// The operands arrive in the canonical array-of-structures layout (one 3x3 complex matrix
+// = 18 contiguous reals).  A block stages its slice of every operand through shared memory
+// with coalesced 16-byte loads, each thread multiplies one pair from shared memory, and
+// the results leave through shared memory with coalesced 16-byte stores: every byte of
+// global memory is touched once, in full sectors.
+#include "lqcd_internal.cuh"
+#include "tune.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+
+// Copy `nreal` reals between global and shared memory with 16-byte accesses (both bases
+// 16-byte aligned) and a scalar tail.
+template <class T>
+__device__ __forceinline__ void copy_g2s(T* __restrict__ dst, const T* __restrict__ src, int nreal) {
+  constexpr int V = 16 / sizeof(T);
+  const int nvec = nreal / V;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) d4[i] = __ldg(s4 + i);
+  for (int i = nvec * V + threadIdx.x; i < nreal; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+template <class T>
+__device__ __forceinline__ void copy_s2g(T* __restrict__ dst, const T* __restrict__ src, int nreal) {
+  constexpr int V = 16 / sizeof(T);
+  const int nvec = nreal / V;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) d4[i] = s4[i];
+  for (int i = nvec * V + threadIdx.x; i < nreal; i += blockDim.x) dst[i] = src[i];
+}
+
+// element (i, j) of op(X): X_ij, or conj(X_ji) for the adjoint
+template <int ADJ, class T>
+__device__ __forceinline__ void elem(const T* x, int i, int j, T& re, T& im) {
+  if (ADJ) { re = x[2 * (3 * j + i)]; im = -x[2 * (3 * j + i) + 1]; }
+  else     { re = x[2 * (3 * i + j)]; im = x[2 * (3 * i + j) + 1]; }
+}
+
+template <class T, int ADJA, int ADJB>
+__global__ void __launch_bounds__(kThreads) k_su3_mul(const T* __restrict__ A, const T* __restrict__ B,
+                                                      T* __restrict__ C, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);
+  T* sB = sA + kThreads * 18;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  copy_g2s(sA, A + base * 18, cnt * 18);
+  copy_g2s(sB, B + base * 18, cnt * 18);
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    T a[18], b[18], c[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) { a[k] = sA[threadIdx.x * 18 + k]; b[k] = sB[threadIdx.x * 18 + k]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          T ar, ai, br, bi;
+          elem<ADJA>(a, i, k, ar, ai);
+          elem<ADJB>(b, k, j, br, bi);
+          re = fma(ar, br, re); re = fma(-ai, bi, re);
+          im = fma(ar, bi, im); im = fma(ai, br, im);
+        }
+        c[2 * (3 * i + j)] = re;
+        c[2 * (3 * i + j) + 1] = im;
+      }
+#pragma unroll
+    for (int k = 0; k < 18; ++k) sA[threadIdx.x * 18 + k] = c[k];
+  }
+  __syncthreads();
+  copy_s2g(C + base * 18, sA, cnt * 18);
+}
+
+template <class T, int ADJ>
+__global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A, const T* __restrict__ b,
+                                                         T* __restrict__ c, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);
+  T* sb = sA + kThreads * 18;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  copy_g2s(sA, A + base * 18, cnt * 18);
+  copy_g2s(sb, b + base * 6, cnt * 6);
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    T a[18], v[6], r[6];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) a[k] = sA[threadIdx.x * 18 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { v[k] = sb[threadIdx.x * 6 + k]; r[k] = 0; }
+    if (ADJ) adj_mat_vec_acc(a, v, r, T(1));
+    else mat_vec_acc(a, v, r, T(1));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sb[threadIdx.x * 6 + k] = r[k];
+  }
+  __syncthreads();
+  copy_s2g(c + base * 6, sb, cnt * 6);
+}
+
+template <class T>
+cudaError_t launch_mul(const void* A, const void* B, void* C, int64_t n, int adjA, int adjB, cudaStream_t s) {
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  const size_t smem = 2 * kThreads * 18 * sizeof(T);
+  const T* a = (const T*)A;
+  const T* b = (const T*)B;
+  T* c = (T*)C;
+  if (!adjA && !adjB) k_su3_mul<T, 0, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n);
+  else if (adjA && !adjB) k_su3_mul<T, 1, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n);
+  else if (!adjA && adjB) k_su3_mul<T, 0, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n);
+  else k_su3_mul<T, 1, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_matvec(const void* A, const void* b, void* c, int64_t n, int adj, cudaStream_t s) {
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  const size_t smem = kThreads * 24 * sizeof(T);
+  if (adj) k_su3_matvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n);
+  else k_su3_matvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n);
+  return cudaGetLastError();
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
+extern "C" lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, int64_t n,
+                                   int adjA, int adjB, lq_prec prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (prec != LQ_F64 && prec != LQ_F32) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "su3_mul_batch supports LQ_F64 and LQ_F32");
+  if ((adjA != 0 && adjA != 1) || (adjB != 0 && adjB != 1)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "adjA/adjB must be 0 or 1");
+  if (n == 0) return LQ_OK;
+  if (!A || !B || !C) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL operand");
+  if (!lq_aligned16(A) || !lq_aligned16(B) || !lq_aligned16(C)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be 16-byte aligned");
+  const size_t bytes = (size_t)n * 18 * lq_prec_bytes(prec);
+  if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "C overlaps A or B");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == LQ_F64 ? launch_mul<double>(A, B, C, n, adjA, adjB, s) : launch_mul<float>(A, B, C, n, adjA, adjB, s);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_mul");
+  return LQ_OK;
+}
+
+extern "C" lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* c, int64_t n,
+                                      int adj, lq_prec prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (prec != LQ_F64 && prec != LQ_F32) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "su3_matvec_batch supports LQ_F64 and LQ_F32");
+  if (adj != 0 && adj != 1) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "adj must be 0 or 1");
+  if (n == 0) return LQ_OK;
+  if (!A || !b || !c) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL operand");
+  if (!lq_aligned16(A) || !lq_aligned16(b) || !lq_aligned16(c)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be 16-byte aligned");
+  const size_t es = lq_prec_bytes(prec);
+  if (overlaps(c, (size_t)n * 6 * es, A, (size_t)n * 18 * es) || overlaps(c, (size_t)n * 6 * es, b, (size_t)n * 6 * es))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "c overlaps A or b");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == LQ_F64 ? launch_matvec<double>(A, b, c, n, adj, s) : launch_matvec<float>(A, b, c, n, adj, s);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_matvec");
+  return LQ_OK;
+}

@@ -1,0 +1,157 @@
+// Device guard, launch-shape autotuner and the deterministic block reduction shared by
+// the kernels.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "lqcd_internal.cuh"
+
+// Makes `device` current for the lifetime of the guard, restoring the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != device) {
+      changed = cudaSetDevice(device) == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+inline bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return true;  // be conservative
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Picks the fastest of `cands` for `key` by timing run(cand) on stream s (one warm-up and
+// three timed launches each), caches the choice in the context.  Without tuning, or while
+// the stream is being captured, the first candidate is used and nothing is cached.
+template <class F>
+lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<TuneEntry>& cands,
+                    cudaStream_t s, F run, TuneEntry* pick) {
+  auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) {
+    *pick = it->second;
+    return LQ_OK;
+  }
+  if (!ctx->tuning || cands.size() == 1 || stream_capturing(s)) {
+    *pick = cands[0];
+    return LQ_OK;
+  }
+  cudaEvent_t e0, e1;
+  LQ_CUDA(ctx, cudaEventCreate(&e0));
+  LQ_CUDA(ctx, cudaEventCreate(&e1));
+  TuneEntry best;
+  best.us = 1e30f;
+  for (const TuneEntry& c : cands) {
+    lq_status st = run(c);
+    if (st) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 3; ++i) run(c);
+    cudaEventRecord(e1, s);
+    cudaError_t err = cudaEventSynchronize(e1);
+    if (err != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return lq_cuda_fail(ctx, err, "tune"); }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    float us = ms * 1000.f / 3.f;
+    if (us < best.us) { best = c; best.us = us; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tune[key] = best;
+  *pick = best;
+  return LQ_OK;
+}
+
+// ------------------------------------------------------------- reductions --------------
+
+// Per right-hand-side scalars of the conjugate-gradient iteration, device resident.
+struct CGScalars {
+  double rr;      // current ||r||^2 of the iterated residual
+  double rr_prev; // ||r||^2 one iteration earlier (denominator of beta)
+  double pAp;     // <p, M p>
+  double alpha, beta;
+  double bb;      // ||b||^2
+  double tol2;    // stop threshold on rr: tol^2 * bb
+  double rhi2;    // ||r||^2 of the last FP64 residual replacement
+  int active;     // 1 while iterating
+  int iters;      // iterations done while active
+  int pad[2];
+};
+
+enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+__device__ __forceinline__ void finish_one(const Reducer& red, int rhs, double total) {
+  CGScalars* s = reinterpret_cast<CGScalars*>(red.finisher_state) + rhs;
+  switch (red.finisher) {
+    case FIN_STORE:
+      red.result[rhs] = total;
+      break;
+    case FIN_ALPHA:
+      s->pAp = total;
+      s->alpha = (s->active && total > 0.0) ? s->rr / total : 0.0;
+      break;
+    case FIN_BETA:
+      if (s->active) {
+        s->iters += 1;
+        s->rr_prev = s->rr;
+        s->rr = total;
+        s->beta = total / s->rr_prev;
+        if (!(total > s->tol2)) s->active = 0;  // apparent convergence (or NaN)
+      }
+      break;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Every thread of the block calls this with its NR per-rhs contributions (rhs0 + r).
+// Partials go to red.partials[rhs][blockIdx.x]; the last block to arrive sums them in
+// block order (deterministic for a given launch shape) and runs the finisher.  No thread
+// ever waits on another block.
+template <int NR>
+__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs) {
+  __shared__ double sm[NR][32];
+  __shared__ int am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    double x = warp_sum(v[r]);
+    if (lane == 0) sm[r][warp] = x;
+  }
+  __syncthreads();
+  const int nbx = gridDim.x;
+  if (warp == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double x = lane < nw ? sm[r][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0 && rhs0 + r < nrhs) red.partials[(size_t)(rhs0 + r) * nbx + blockIdx.x] = x;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned total = gridDim.x * gridDim.y;
+    unsigned prev = atomicAdd(red.counter, 1u);
+    am_last = (prev == total - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int rhs = warp; rhs < nrhs; rhs += nw) {
+    double x = 0.0;
+    for (int b = lane; b < nbx; b += 32) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
+    x = warp_sum(x);
+    if (lane == 0) finish_one(red, rhs, x);
+  }
+  if (threadIdx.x == 0) *red.counter = 0u;
+}

@@ -105,3 +105,13 @@ def test_multi_rhs_is_columnwise():
     out = dslash.dslash_eo_multi(U, chi, dims, 0)
     for k in range(3):
         assert np.array_equal(out[k], dslash.dslash_eo(U, chi[k], dims, 0))
+
+
+def test_sitewise_dslash_matches_stencil():
+    dims = (4, 6, 2, 4)
+    U = synth.gauge_field(dims, "haar", seed=36)
+    for p in (0, 1):
+        v = _cb_vec(dims, 37 + p)
+        full = dslash.dslash_eo(U, v, dims, p)
+        sites = np.arange(0, full.shape[0], 7)
+        assert np.abs(dslash.dslash_eo_sites(U, v, dims, p, sites) - full[sites]).max() < 1e-13
