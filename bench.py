@@ -1,0 +1,515 @@
+#!/usr/bin/env python
+"""Staggered Dslash throughput on one GB300 (GFLOP/s at 570 flops per site, HBM GB/s and
+its fraction of the measured copy bandwidth), plus the CG time to a 1e-10 residual with
+mixed precision against FP64.
+
+Workload (one "step"): 100 applications of the full staggered Dslash D = D_eo + D_oe on a
+16^3 x 32 lattice (two half-Dslash launches each: t = D_oe chi, out = D_eo t), links
+exp(i 0.3 H) re-projected to SU(3), Gaussian vectors, seeded.  To keep the timed region
+honest about HBM, the launches cycle over a ring of K device copies of the packed links
+and vectors whose total size exceeds three times the L2 cache, so no launch finds its
+links in L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32 --recon 18]
+    python bench.py --impl reference       # the FP64 numpy oracle on the host cores
+
+Under torchrun every rank runs its own replica (independent lattices, no collective on the
+data path); the value is the flops of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s & HBM GB/s vs ~8 TB/s; mixed-prec CG time to 1e-10 vs FP64"
+DIMS = (16, 16, 16, 32)
+APPS = 100                 # Dslash applications per step
+FLOPS_PER_SITE = 570
+BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+
+# DRAM bytes per k_dslash launch from the ncu capture summarised under profiles/ (key:
+# storage format), with the hash of the kernel sources it was taken on.  A changed kernel
+# makes the figure stale and the bench reports null.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = ("paper_1309_0551_gb300/csrc/dslash_kernel.cuh",
+                  "paper_1309_0551_gb300/csrc/lqcd_internal.cuh")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def site_bytes(prec, recon, vec):
+    """Algorithmic bytes per output site of a half Dslash: 8 links read once, the input
+    vector read once (its 8-fold neighbour reuse served on chip), the output written once."""
+    return 8 * recon * BYTES[prec] + 2 * 6 * BYTES[vec]
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--prec", default="f32", choices=["f64", "f32", "bf16", "f16"])
+    p.add_argument("--recon", type=int, default=18, choices=[18, 12])
+    p.add_argument("--vec", default=None, help="vector storage (default: f64 for f64 links, else f32)")
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cg", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ distributed -------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if use_cuda else "gloo")
+    return dist
+
+
+def max_over_ranks(dist, value, device=None):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks ------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), f[3], f[4:]))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU arm -----------
+
+def make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2):
+    import torch
+    import synth
+    Vh = synth.volume(dims) // 2
+    chi = synth.fermion_field(dims, 1, seed=seed)
+    gauges = [lq.lq_gauge_pack(ctx, dims, U_dev, prec, recon) for _ in range(K)]
+    host = torch.from_numpy(chi)
+
+    def vec_tensor(src=None):
+        if vec == "f64":
+            return (src.cuda() if src is not None else torch.empty((1, Vh, 3), dtype=torch.complex128, device="cuda"))
+        if vec == "f32":
+            return (src.to(torch.complex64).cuda() if src is not None
+                    else torch.empty((1, Vh, 3), dtype=torch.complex64, device="cuda"))
+        dt = torch.bfloat16 if vec == "bf16" else torch.float16
+        if src is not None:
+            return torch.view_as_real(src).to(dt).contiguous().cuda()
+        return torch.empty((1, Vh, 3, 2), dtype=dt, device="cuda")
+
+    ins = [vec_tensor(host) for _ in range(K)]
+    ts = [vec_tensor() for _ in range(K)]
+    outs = [vec_tensor() for _ in range(K)]
+    return gauges, ins, ts, outs
+
+
+def ring_size(bytes_per_copy, l2_bytes):
+    """Copies so that the ring holds > 3x L2; a multiple of 4, so that applications that
+    share a copy always fall on the same one of the two streams."""
+    k = max(4, -(-3 * l2_bytes // bytes_per_copy))
+    return -(-k // 4) * 4
+
+
+def run_step(lq, ctx, gauges, ins, ts, outs, vec_code, streams, apps=APPS):
+    """One step: `apps` applications of D.  Application a runs on streams[a % S] (the
+    applications are independent; the two halves of one are ordered on its stream), and
+    half-Dslash launch h uses ring copy h mod K.  Returns the number of launches."""
+    K = len(gauges)
+    S = len(streams)
+    h = 0
+    for a in range(apps):
+        s = streams[a % S]
+        c = h % K
+        c2 = (h + 1) % K
+        lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, 1, vec_code, s)      # t = D_oe chi
+        lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, 1, vec_code, s)    # out = D_eo t
+        h += 2
+    return 2 * apps
+
+
+class GraphStep:
+    """A step captured once as a CUDA graph (after an eager run that tunes launch shapes)
+    and replayed; `fn(streams)` issues the step's launches on the given streams."""
+
+    def __init__(self, torch, fn, nstreams=2):
+        self.torch = torch
+        fn([torch.cuda.current_stream()])          # eager: tunes, checks
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        side = [torch.cuda.Stream() for _ in range(nstreams - 1)]
+        with torch.cuda.graph(self.graph):
+            main = torch.cuda.current_stream()
+            for s in side:
+                s.wait_stream(main)
+            self.launches = fn([main] + side)
+            for s in side:
+                main.wait_stream(s)
+        torch.cuda.synchronize()
+
+    def __call__(self):
+        self.graph.replay()
+        return self.launches
+
+
+def time_steps(torch, fn, steps, warmup, stream, dist=None, device=None, sampler=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    e0.record(stream)
+    launches = 0
+    for _ in range(steps):
+        launches += fn()
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop() if sampler else None
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(dist, ms, device), launches, clocks
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(dims, seconds=12.0):
+    """The oracle (numpy FP64, one thread of work per call) timed on the host: half Dslash
+    applications at the benchmark's lattice size until about `seconds` have passed."""
+    import synth
+    from oracle import dslash as odslash
+    U = synth.gauge_field(dims, "near_identity", seed=3, eps=0.3)
+    chi = synth.fermion_field(dims, 1, seed=2)[0]
+    Vh = synth.volume(dims) // 2
+    n, t0 = 0, time.perf_counter()
+    while True:
+        odslash.dslash_eo(U, chi, dims, 1 - (n & 1))
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return {"value": round(n * Vh * FLOPS_PER_SITE / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n} half-Dslash applications of the FP64 numpy oracle on the "
+                      f"{'x'.join(map(str, dims))} lattice ({dt:.1f} s)"}
+
+
+def run_variants(lq, ctx, torch, U_dev, l2, stream):
+    out = {}
+    forms = [("f64", 18, "f64"), ("f64", 12, "f64"), ("f32", 18, "f32"), ("f32", 12, "f32"),
+             ("bf16", 18, "bf16"), ("bf16", 12, "bf16"), ("f16", 12, "f16")]
+    peak, _ = measured_peak()
+    Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
+    for prec, recon, vec in forms:
+        sb = site_bytes(prec, recon, vec)
+        K = ring_size(Vh * sb, l2)
+        gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K)
+        vc = lq.PREC[vec]
+        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20))
+        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+        del g
+        us = ms * 1000.0 / launches
+        gbs = Vh * sb / us / 1e3
+        out[f"{prec}/{recon}/{vec}"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1),
+                                       "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                                       "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+        del gauges, ins, ts, outs
+        torch.cuda.empty_cache()
+    # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
+    import synth
+    n = 4 * 2 * Vh
+    A = torch.from_numpy(synth.haar_su3(synth.rng(9), n))
+    b = torch.from_numpy(synth.complex_gaussian(synth.rng(10), (n, 3)))
+    for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
+        per = n * 30 * BYTES[prec]
+        K = ring_size(per, l2)
+        As = [A.to(dt).cuda() for _ in range(K)]
+        bs = [b.to(dt).cuda() for _ in range(K)]
+        cs = [torch.empty_like(bs[0]) for _ in range(K)]
+        for adj in (0, 1):
+            def step(ss):
+                for i in range(20):
+                    lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[0])
+                return 20
+            g = GraphStep(torch, step, 1)
+            ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = per / us / 1e3
+            out[f"su3_matvec/{prec}/adj{adj}"] = {"gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                  "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
+        del As, bs, cs
+    return out
+
+
+def run_cg(lq, ctx, torch):
+    """32^4, Haar links, m = 0.01, Gaussian source: FP64 CG against mixed precision."""
+    import synth
+    dims, mass = (32, 32, 32, 32), 0.01
+    U = torch.from_numpy(synth.gauge_field(dims, "haar", seed=4)).cuda()
+    b = torch.from_numpy(synth.fermion_field(dims, 1, seed=5)).cuda()
+    x = torch.empty_like(b)
+    hi = lq.lq_gauge_pack(ctx, dims, U, "f64", 18)
+    res = {"workload": "32^4 Haar SU(3), m=0.01, Gaussian source, tol 1e-10 (FP64 true residual)"}
+    for name, prec, recon in (("fp64", None, 18), ("mixed_f32_12", "f32", 12), ("mixed_f16_12", "f16", 12),
+                              ("mixed_bf16_12", "bf16", 12)):
+        lo = lq.lq_gauge_pack(ctx, dims, U, prec, recon) if prec else None
+        try:  # a short solve first: tunes the launch shapes outside the timed solve
+            lq.cg_solve(ctx, hi, lo, mass, b, x, 1, tol=1e-10, maxiter=200)
+        except lq.LQError:
+            pass
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            st = lq.cg_solve(ctx, hi, lo, mass, b, x, 1, tol=1e-10, maxiter=20000)[0]
+            ok = True
+        except lq.LQError as e:
+            st, ok = e.stats[0], False
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"seconds": round(dt, 4), "iters": st["iters"], "reliable_updates": st["reliable_updates"],
+                     "true_rel_resid": st["true_rel_resid"], "converged": ok}
+    if res["fp64"]["converged"]:
+        for k in ("mixed_f32_12", "mixed_f16_12", "mixed_bf16_12"):
+            if res[k]["converged"]:
+                res[k]["speedup_vs_fp64"] = round(res["fp64"]["seconds"] / res[k]["seconds"], 2)
+    return res
+
+
+def run_ours(args):
+    import torch
+    import paper_1309_0551_gb300 as lq
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local)
+    lq.load()  # raises if the library has not been built (__graft_entry__.build())
+    ctx = lq.Context(local)
+    stream = torch.cuda.current_stream()
+    prec, recon = args.prec, args.recon
+    vec = args.vec or ("f64" if prec == "f64" else "f32")
+    vc = lq.PREC[vec]
+    props = torch.cuda.get_device_properties(local)
+    l2 = int(getattr(props, "L2_cache_size", 128 << 20))
+    Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
+    sb = site_bytes(prec, recon, vec)
+    K = ring_size(Vh * sb, l2)
+    U_host = synth.gauge_field(DIMS, "near_identity", seed=3 + rank, eps=0.3)
+    U_dev = torch.from_numpy(U_host).cuda()
+    gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K, seed=2 + rank)
+
+    # ---- device-resident throughput
+    step = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss))
+    sampler = ClockSampler(local)
+    ms, launches, clocks = time_steps(torch, step, args.steps, args.warmup, stream, dist, device, sampler)
+    flops = args.steps * APPS * 2 * Vh * FLOPS_PER_SITE * world
+    value = flops / (ms * 1e-3) / 1e9
+    us_per_launch = ms * 1000.0 / launches
+    achieved = Vh * sb / us_per_launch / 1e3  # GB/s
+    peak, peak_kind = measured_peak()
+    key = f"{prec}/{recon}/{vec}"
+    traffic = None
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_hash():
+        traffic = NCU_TRAFFIC[key][0]
+
+    # ---- end to end: pinned host inputs copied in, outputs copied out, every step
+    host_in = [torch.empty_like(t, device="cpu").pin_memory() for t in ins]
+    for h, t in zip(host_in, ins):
+        h.copy_(t)
+    host_out = [torch.empty_like(t, device="cpu").pin_memory() for t in outs]
+
+    def e2e_step():
+        for h, t in zip(host_in, ins):
+            t.copy_(h, non_blocking=True)
+        n = step()
+        for h, t in zip(host_out, outs):
+            h.copy_(t, non_blocking=True)
+        return n
+
+    e2e_steps = max(1, args.steps // 2)
+    ms_e2e, _, _ = time_steps(torch, e2e_step, e2e_steps, min(args.warmup, 3), stream, dist, device)
+    e2e_val = e2e_steps * APPS * 2 * Vh * FLOPS_PER_SITE * world / (ms_e2e * 1e-3) / 1e9
+    vbytes = ins[0].numel() * ins[0].element_size()
+
+    extra = {}
+    if rank == 0 and not args.no_variants:
+        extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream)
+    if rank == 0 and not args.no_cg:
+        extra["cg"] = run_cg(lq, ctx, torch)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == "f64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": "staggered Dslash, 16^3x32 lattice, links exp(i*0.3*H) on SU(3), "
+                               f"{APPS} full-D applications per step",
+                   "lattice": "16x16x16x32", "link_storage": f"{prec}/{recon}-real", "vector_storage": vec,
+                   "l2": f"inputs larger than L2: ring of {K} device copies of links and vectors "
+                         f"({K * Vh * sb / 1e6:.0f} MB) cycled across launches",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_dslash", "bytes_per_launch": Vh * sb,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                     "us_per_launch": round(us_per_launch, 3)},
+        "e2e": {"value": round(e2e_val, 1), "unit": "GFLOP/s", "h2d_bytes_per_step": K * vbytes,
+                "d2h_bytes_per_step": K * vbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extra)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(DIMS)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm -----
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is one half-Dslash application
+    of the FP64 numpy oracle on the benchmark lattice (a bounded sample of the workload)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    from oracle import dslash as odslash
+    U = synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)
+    chi = synth.fermion_field(DIMS, 1, seed=2)[0]
+    Vh = synth.volume(DIMS) // 2
+    for i in range(args.warmup):
+        odslash.dslash_eo(U, chi, DIMS, 1 - (i & 1))
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        odslash.dslash_eo(U, chi, DIMS, 1 - (i & 1))
+    dt = time.perf_counter() - t0
+    value = args.steps * Vh * FLOPS_PER_SITE / dt / 1e9
+    sample = f"{args.steps} half-Dslash applications (one per step) on the 16x16x16x32 lattice"
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1000 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "staggered Dslash, 16^3x32 lattice, links exp(i*0.3*H) on SU(3)",
+                   "lattice": "16x16x16x32", "implementation": "FP64 numpy oracle on the host"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
