@@ -164,6 +164,31 @@ lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, 
                    const void* b, void* x, int nrhs, const lq_cg_params* params,
                    lq_cg_stats* stats, lq_stream stream);
 
+/* Allocation-free variant of cg_solve.  The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate GPU memory when they solve -- for example code
+ * running inside a host framework or plugin that forbids cudaMalloc/cudaFree on its
+ * threads, or a loop under a fixed memory budget that must not grow or synchronise the
+ * device through an allocation.
+ *   Same arguments, results and statuses as cg_solve.  Its scratch space (work vectors,
+ *   per-rhs scalars, reduction partials) is a fixed 32 MiB array inside the library
+ *   image, so every GPU that loads the library holds those 32 MiB until the process
+ *   exits.  It calls no cudaMalloc, cudaFree or cudaMallocHost, and creates no stream,
+ *   event or graph: the solve runs as plain kernel launches on `stream`, synchronising it
+ *   at each check.  Launch shapes come from the context's tuning table when an earlier
+ *   call (e.g. cg_solve with the same gauges) filled it, else fixed defaults.
+ *   Limit: (4 inner vectors, 5 with U_lo) * nrhs * Vh * 48 bytes (24 with U_lo) + 2 FP64
+ *   vectors of nrhs * Vh * 48 bytes + nrhs * Vh/64 * 8 bytes of partials must fit in
+ *   32 MiB (e.g. a 16^4 lattice with one right-hand side); larger problems get
+ *   LQ_ERR_INVALID_ARG with a message naming the sizes.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *   and caches it; make that first call before any stream capture.
+ *   All calls share the one array and each leaves its contents behind (the call clears
+ *   what must start at zero): calls whose GPU work overlaps -- on different streams,
+ *   threads or contexts of the same device -- race on it and give wrong results. */
+lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, double mass,
+                           const void* b, void* x, int nrhs, const lq_cg_params* params,
+                           lq_cg_stats* stats, lq_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,8 @@ def load(path: str | None = None):
         "dslash_eo": ([P, P, P, P, I, I, I, P], I),
         "cg_solve": ([P, P, P, D, P, P, I, ctypes.POINTER(lq_cg_params),
                       ctypes.POINTER(lq_cg_stats), P], I),
+        "cg_solve_noalloc": ([P, P, P, D, P, P, I, ctypes.POINTER(lq_cg_params),
+                              ctypes.POINTER(lq_cg_stats), P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -201,15 +203,12 @@ def su3_matvec_batch(ctx: Context, A, b, c, n=None, adj=0, prec=None, stream=Non
                                        int(prec), _stream(stream)))
 
 
-def cg_solve(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float, b, x, nrhs: int = 1,
-             tol=1e-10, maxiter=10000, reliable_every=100, delta=0.1, check_every=20, stream=None):
-    """Solve (m^2 - D_eo D_oe) x = b on even sites; returns a list of per-rhs stats dicts.
-    Raises LQError on failure (including LQ_ERR_NOT_CONVERGED)."""
+def _cg_call(fn, ctx, U_hi, U_lo, mass, b, x, nrhs, tol, maxiter, reliable_every, delta,
+             check_every, stream):
     params = lq_cg_params(float(tol), int(maxiter), int(reliable_every), float(delta), int(check_every))
     stats = (lq_cg_stats * int(nrhs))()
-    st = ctx.lib.cg_solve(ctx.handle, U_hi.handle, None if U_lo is None else U_lo.handle,
-                          float(mass), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(params),
-                          stats, _stream(stream))
+    st = fn(ctx.handle, U_hi.handle, None if U_lo is None else U_lo.handle,
+            float(mass), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(params), stats, _stream(stream))
     out = [dict(iters=s.iters, reliable_updates=s.reliable_updates,
                 true_rel_resid=s.true_rel_resid, seconds=s.seconds) for s in stats]
     if st != 0:
@@ -217,3 +216,21 @@ def cg_solve(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float, b, x, n
         err.stats = out
         raise err
     return out
+
+
+def cg_solve(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float, b, x, nrhs: int = 1,
+             tol=1e-10, maxiter=10000, reliable_every=100, delta=0.1, check_every=20, stream=None):
+    """Solve (m^2 - D_eo D_oe) x = b on even sites; returns a list of per-rhs stats dicts.
+    Raises LQError on failure (including LQ_ERR_NOT_CONVERGED)."""
+    return _cg_call(ctx.lib.cg_solve, ctx, U_hi, U_lo, mass, b, x, nrhs, tol, maxiter,
+                    reliable_every, delta, check_every, stream)
+
+
+def cg_solve_noalloc(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float, b, x,
+                     nrhs: int = 1, tol=1e-10, maxiter=10000, reliable_every=100, delta=0.1,
+                     check_every=20, stream=None):
+    """cg_solve for callers that cannot allocate GPU memory when they solve: scratch in the
+    library's fixed 32 MiB device array, no allocation, stream, event or graph creation.
+    Calls whose GPU work overlaps share that array and race."""
+    return _cg_call(ctx.lib.cg_solve_noalloc, ctx, U_hi, U_lo, mass, b, x, nrhs, tol, maxiter,
+                    reliable_every, delta, check_every, stream)

@@ -293,7 +293,8 @@ struct GraphHolder {
   }
 };
 
-lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* converged_all) {
+lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* converged_all,
+                     bool use_graph = true) {
   lq_context* ctx = S.ctx;
   const int n = S.nrhs;
   const double tol2 = P.tol * P.tol;
@@ -351,7 +352,7 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     if (total >= P.maxiter) break;
     if (any_active) {
       // ---- a block of inner iterations
-      if (first) {
+      if (first || !use_graph) {
         for (int k = 0; k < block; ++k) {
           st = iteration(S);
           if (st) return st;
@@ -522,6 +523,123 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   cudaEventRecord(ev, S.s);
   cudaStreamWaitEvent(user, ev, 0);
   cudaEventDestroy(ev);
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int i = 0; i < nrhs; ++i) stats[i].seconds = secs;
+  if (st) return st;
+  if (!converged) return lq_fail(ctx, LQ_ERR_NOT_CONVERGED, "CG did not reach tol %.3g within %d iterations",
+                                 params->tol, params->maxiter);
+  return LQ_OK;
+}
+
+// ------------------------------------------------------------- allocation-free solve ---
+//
+// Some callers may not allocate GPU memory at the point where they solve: code running
+// under a caller-managed memory pool or budget, plugins whose host framework forbids
+// cudaMalloc/cudaFree on its worker threads, or loops that must not synchronise the
+// device the way cudaMalloc/cudaFree can.  cg_solve_noalloc serves them: it runs the same
+// solver as cg_solve, but its scratch space (work vectors, per-rhs scalars, reduction
+// partials) lives in the fixed array below, and it creates no stream, event or graph.
+// The array is part of the library image: every GPU that loads the library holds these
+// bytes until the process exits.
+
+static constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_cg_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {};
+
+// Device address of the static array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per device with
+// cudaGetSymbolAddress (which needs that device current) and cached.
+static lq_status noalloc_scratch(lq_context* ctx, void** out) {
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= 64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_cg_noalloc_scratch);
+    if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "cudaGetSymbolAddress(g_cg_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LQ_OK;
+}
+
+extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, double mass,
+                                      const void* b, void* x, int nrhs, const lq_cg_params* params,
+                                      lq_cg_stats* stats, lq_stream stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (!U_hi || !params) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_hi and params are required");
+  if (U_hi->prec != LQ_F64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_hi must be an LQ_F64 gauge");
+  if (U_lo) {
+    if (U_lo->prec == LQ_F64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_lo must be LQ_F32, LQ_BF16 or LQ_F16");
+    for (int i = 0; i < 4; ++i)
+      if (U_lo->dims[i] != U_hi->dims[i]) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_lo and U_hi lattices differ");
+  }
+  if (!b || !x || !lq_aligned16(b) || !lq_aligned16(x))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "b and x must be non-NULL 16-byte aligned device pointers");
+  if (b == x) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "b and x must be distinct");
+  if (nrhs < 1 || nrhs > 16) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  if (!(params->tol > 0.0) || params->maxiter < 1 || params->check_every < 1 || params->reliable_every < 1 ||
+      !(params->delta >= 0.0 && params->delta < 1.0))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad CG parameters");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+
+  Solver S{};
+  S.ctx = ctx;
+  S.Uhi = U_hi;
+  S.Ulo = U_lo ? U_lo : U_hi;
+  S.mixed = U_lo != nullptr;
+  S.vp = S.mixed ? LQ_F32 : LQ_F64;
+  S.mass = mass;
+  S.nrhs = nrhs;
+  S.Vh = U_hi->Vh;
+  S.b = (const double*)b;
+  S.x = (double*)x;
+  S.nbx = (S.Vh + kBlas - 1) / kBlas;
+  if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
+  S.nblocks_max = (S.Vh + 63) / 64;
+  if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
+  const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
+  const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +
+                      (size_t)nrhs * S.nblocks_max * sizeof(double) + 12 * 256;
+  if (need > kNoAllocScratchBytes)
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG,
+                   "cg_solve_noalloc: %d right-hand sides on %d sites per parity need %zu bytes of scratch, "
+                   "more than its fixed %zu-byte array; use cg_solve", nrhs, S.Vh, need, kNoAllocScratchBytes);
+  void* base = nullptr;
+  lq_status st = noalloc_scratch(ctx, &base);
+  if (st) return st;
+  Arena A{(char*)base};
+  S.xl = S.mixed ? A.take(vin) : x;
+  S.r = A.take(vin);
+  S.p = A.take(vin);
+  S.Ap = A.take(vin);
+  S.t = A.take(vin);
+  S.rhi = (double*)A.take(v64);
+  S.thi = (double*)A.take(v64);
+  S.sc = (CGScalars*)A.take(sizeof(CGScalars) * nrhs);
+  S.result = (double*)A.take(sizeof(double) * nrhs);
+  S.counter = (unsigned int*)A.take(sizeof(unsigned int));
+  S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  if (A.off > kNoAllocScratchBytes) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
+  CGScalars host_scalars[16];  // pageable host copy of the per-rhs scalars
+  S.sc_host = host_scalars;
+  S.s = (cudaStream_t)stream;  // the caller's stream: nothing is created
+
+  // The array keeps the previous call's contents; the reduction counter must start at 0
+  // (every other scratch word is written before it is read).
+  LQ_CUDA(ctx, cudaMemsetAsync(S.counter, 0, sizeof(unsigned int), S.s));
+  // Launch shapes come from the context's tuning table when an earlier call tuned them,
+  // else the defaults: no timing runs here.
+  const bool tuning = ctx->tuning;
+  ctx->tuning = false;
+  int converged = 0;
+  st = run_solver(S, *params, stats, &converged, /*use_graph=*/false);
+  ctx->tuning = tuning;
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
     for (int i = 0; i < nrhs; ++i) stats[i].seconds = secs;
