@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--prec", default="f32", choices=["f64", "f32", "bf16", "f16"])
     p.add_argument("--recon", type=int, default=18, choices=[18, 12])
     p.add_argument("--vec", default=None, help="vector storage (default: f64 for f64 links, else f32)")
+    p.add_argument("--streams", type=int, default=4,
+                   help="independent applications in flight (graph branches)")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -181,11 +183,12 @@ def make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2):
     return gauges, ins, ts, outs
 
 
-def ring_size(bytes_per_copy, l2_bytes):
-    """Copies so that the ring holds > 3x L2; a multiple of 4, so that applications that
-    share a copy always fall on the same one of the two streams."""
-    k = max(4, -(-3 * l2_bytes // bytes_per_copy))
-    return -(-k // 4) * 4
+def ring_size(bytes_per_copy, l2_bytes, nstreams=4):
+    """Copies so that the ring holds > 3x L2; a multiple of 2*nstreams, so that the
+    applications that share a copy always run on the same stream (in order)."""
+    m = 2 * nstreams
+    k = max(m, -(-3 * l2_bytes // bytes_per_copy))
+    return -(-k // m) * m
 
 
 def run_step(lq, ctx, gauges, ins, ts, outs, vec_code, streams, apps=APPS):
@@ -284,7 +287,7 @@ def cpu_baseline(dims, seconds=12.0):
                       f"{'x'.join(map(str, dims))} lattice ({dt:.1f} s)"}
 
 
-def run_variants(lq, ctx, torch, U_dev, l2, stream):
+def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
     out = {}
     forms = [("f64", 18, "f64"), ("f64", 12, "f64"), ("f32", 18, "f32"), ("f32", 12, "f32"),
              ("bf16", 18, "bf16"), ("bf16", 12, "bf16"), ("f16", 12, "f16")]
@@ -292,10 +295,10 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream):
     Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
     for prec, recon, vec in forms:
         sb = site_bytes(prec, recon, vec)
-        K = ring_size(Vh * sb, l2)
+        K = ring_size(Vh * sb, l2, nstreams)
         gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K)
         vc = lq.PREC[vec]
-        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20))
+        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
         ms, launches, _ = time_steps(torch, g, 10, 3, stream)
         del g
         us = ms * 1000.0 / launches
@@ -385,13 +388,13 @@ def run_ours(args):
     l2 = int(getattr(props, "L2_cache_size", 128 << 20))
     Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
     sb = site_bytes(prec, recon, vec)
-    K = ring_size(Vh * sb, l2)
+    K = ring_size(Vh * sb, l2, args.streams)
     U_host = synth.gauge_field(DIMS, "near_identity", seed=3 + rank, eps=0.3)
     U_dev = torch.from_numpy(U_host).cuda()
     gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K, seed=2 + rank)
 
     # ---- device-resident throughput
-    step = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss))
+    step = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss), args.streams)
     sampler = ClockSampler(local)
     ms, launches, clocks = time_steps(torch, step, args.steps, args.warmup, stream, dist, device, sampler)
     flops = args.steps * APPS * 2 * Vh * FLOPS_PER_SITE * world
@@ -425,7 +428,7 @@ def run_ours(args):
 
     extra = {}
     if rank == 0 and not args.no_variants:
-        extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream)
+        extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream, args.streams)
     if rank == 0 and not args.no_cg:
         extra["cg"] = run_cg(lq, ctx, torch)
     line = {
@@ -457,6 +460,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line["config"]["streams"] = args.streams
+    line["config"]["launch_shape"] = [l for l in ctx.tune_report().splitlines()
+                                      if f"g={prec}/{recon} v={vec} dims=16x16x16x32 nrhs=1" in l]
     line.update(extra)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(DIMS)

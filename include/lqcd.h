@@ -177,7 +177,7 @@ lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, 
  *   at each check.  Launch shapes come from the context's tuning table when an earlier
  *   call (e.g. cg_solve with the same gauges) filled it, else fixed defaults.
  *   Limit: (4 inner vectors, 5 with U_lo) * nrhs * Vh * 48 bytes (24 with U_lo) + 2 FP64
- *   vectors of nrhs * Vh * 48 bytes + nrhs * Vh/64 * 8 bytes of partials must fit in
+ *   vectors of nrhs * Vh * 48 bytes + nrhs * Vh/16 * 8 bytes of partials must fit in
  *   32 MiB (e.g. a 16^4 lattice with one right-hand side); larger problems get
  *   LQ_ERR_INVALID_ARG with a message naming the sizes.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)

@@ -478,7 +478,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.x = (double*)x;
   S.nbx = (S.Vh + kBlas - 1) / kBlas;
   if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
-  S.nblocks_max = (S.Vh + 63) / 64;
+  S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
@@ -601,7 +601,7 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.x = (double*)x;
   S.nbx = (S.Vh + kBlas - 1) / kBlas;
   if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
-  S.nblocks_max = (S.Vh + 63) / 64;
+  S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +

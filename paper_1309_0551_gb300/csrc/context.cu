@@ -63,6 +63,17 @@ extern "C" lq_status lq_create(lq_context** out, int device) {
   ctx->l2_bytes = prop.l2CacheSize;
   const char* env = getenv("LQCD_TUNE");
   ctx->tuning = !(env && env[0] == '0');
+  // "block,rhs_tile,threads_per_site", e.g. "128,1,2": every Dslash launch whose right-hand
+  // side count admits that tile uses this shape instead of the tuned one.
+  const char* shape = getenv("LQCD_DSLASH_SHAPE");
+  if (shape) {
+    int b = 0, t = 0, p = 0;
+    if (sscanf(shape, "%d,%d,%d", &b, &t, &p) == 3 && b >= 64 && b <= 256 && b % 32 == 0) {
+      ctx->forced.block = b;
+      ctx->forced.rhs_tile = t;
+      ctx->forced.tps = p;
+    }
+  }
   *out = ctx;
   return LQ_OK;
 }
@@ -73,6 +84,7 @@ extern "C" lq_status lq_destroy(lq_context* ctx) {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->flush) cudaFree(ctx->flush);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   }
   delete ctx;
@@ -90,8 +102,8 @@ extern "C" lq_status lq_tune_report(const lq_context* ctx, char* buf, size_t len
   std::string s;
   for (const auto& kv : ctx->tune) {
     char line[256];
-    snprintf(line, sizeof line, "%s block=%d rhs_tile=%d us=%.3f\n", kv.first.c_str(),
-             kv.second.block, kv.second.rhs_tile, kv.second.us);
+    snprintf(line, sizeof line, "%s block=%d rhs_tile=%d tps=%d us=%.3f\n", kv.first.c_str(),
+             kv.second.block, kv.second.rhs_tile, kv.second.tps, kv.second.us);
     s += line;
   }
   if (needed) *needed = s.size() + 1;

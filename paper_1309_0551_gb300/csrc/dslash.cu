@@ -38,8 +38,8 @@ static std::string dslash_key(const lq_gauge* g, lq_prec vp, int nrhs) {
   return buf;
 }
 
-// Candidate launch shapes, default first.  FP64 tiles stop at 4 right-hand sides (eight
-// FP64 accumulators per rhs already cost 12 registers each).
+// Candidate launch shapes (block, rhs tile, threads per site), default first.  FP64
+// tiles stop at 4 right-hand sides (FP64 accumulators cost two registers each).
 static std::vector<TuneEntry> dslash_candidates(lq_prec gp, int nrhs) {
   std::vector<int> tiles;
   for (int t : {1, 2, 4, 8})
@@ -48,15 +48,19 @@ static std::vector<TuneEntry> dslash_candidates(lq_prec gp, int nrhs) {
   for (int t : tiles)
     if (t <= (gp == LQ_F64 ? 2 : 4)) first_tile = t;
   std::vector<TuneEntry> c;
-  c.push_back(TuneEntry{128, first_tile, 0.f});
+  TuneEntry d;
+  d.block = 128; d.rhs_tile = first_tile; d.tps = 1;
+  c.push_back(d);
   for (int t : tiles)
-    for (int b : {64, 128, 256})
-      if (!(b == 128 && t == first_tile)) c.push_back(TuneEntry{b, t, 0.f});
+    for (int tps : {1, 2, 4})
+      for (int b : {64, 128, 256}) {
+        if (!dslash_shape_ok(t, tps) || (b == 128 && t == first_tile && tps == 1)) continue;
+        TuneEntry e;
+        e.block = b; e.rhs_tile = t; e.tps = tps;
+        c.push_back(e);
+      }
   return c;
 }
-
-// Smallest block size any candidate uses (bounds the reduction partials per rhs).
-int dslash_min_block() { return 64; }
 
 static DslashKArgs make_kargs(const DslashArgs& a) {
   DslashKArgs k;
@@ -89,21 +93,27 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   plain.c = 1.0;
   plain.reduce = RED_NONE;
   TuneEntry pick;
-  lq_status st = tune_pick(
-      ctx, dslash_key(a.U, a.vec_prec, a.nrhs), dslash_candidates(a.U->prec, a.nrhs), s,
-      [&](const TuneEntry& c) -> lq_status {
-        cudaError_t e = fn(plain, a.vec_prec, c.block, c.rhs_tile, s);
-        if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash (tuning)");
-        return LQ_OK;
-      },
-      &pick);
-  if (st) return st;
+  const TuneEntry& f = ctx->forced;
+  if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
+      !(a.U->prec == LQ_F64 && f.rhs_tile > 4)) {
+    pick = f;
+  } else {
+    lq_status st = tune_pick(
+        ctx, dslash_key(a.U, a.vec_prec, a.nrhs), dslash_candidates(a.U->prec, a.nrhs), s,
+        [&](const TuneEntry& c) -> lq_status {
+          cudaError_t e = fn(plain, a.vec_prec, c.block, c.rhs_tile, c.tps, s);
+          if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash (tuning)");
+          return LQ_OK;
+        },
+        &pick);
+    if (st) return st;
+  }
   if (a.reduce != RED_NONE) {
-    int nbx = (k.G.Vh + pick.block - 1) / pick.block;
+    int nbx = (int)(((long long)k.G.Vh * pick.tps + pick.block - 1) / pick.block);
     if (!a.red || nbx > a.red->nblocks_max)
       return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
   }
-  cudaError_t e = fn(k, a.vec_prec, pick.block, pick.rhs_tile, s);
+  cudaError_t e = fn(k, a.vec_prec, pick.block, pick.rhs_tile, pick.tps, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash");
   return LQ_OK;
 }

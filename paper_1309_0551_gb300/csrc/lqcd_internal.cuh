@@ -19,6 +19,7 @@ struct TuneEntry {
   int block = 0;      // threads per block
   int rhs_tile = 1;   // right-hand sides per thread (Dslash)
   float us = 0.f;     // best measured time
+  int tps = 1;        // threads per output site (Dslash)
 };
 
 struct lq_context {
@@ -33,6 +34,9 @@ struct lq_context {
   size_t scratch_bytes = 0;
   void* host_pinned = nullptr;  // small pinned buffer for convergence checks
   size_t host_pinned_bytes = 0;
+  void* flush = nullptr;        // buffer larger than L2, written between tuning timings
+  size_t flush_bytes = 0;
+  TuneEntry forced;             // Dslash launch shape forced by LQCD_DSLASH_SHAPE (block 0: none)
   std::mutex mu;
 };
 
@@ -246,6 +250,13 @@ template <lq_prec P> struct VecT;
 template <> struct VecT<LQ_F64> {
   using real = double;
   static constexpr size_t bytes_per_site = 48;
+  __device__ __forceinline__ static void load_c(const void* base, size_t site, int c, double* v) {
+    double2 w = __ldg(reinterpret_cast<const double2*>(base) + 3 * site + c);
+    v[0] = w.x; v[1] = w.y;
+  }
+  __device__ __forceinline__ static void store_c(void* base, size_t site, int c, const double* v) {
+    reinterpret_cast<double2*>(base)[3 * site + c] = make_double2(v[0], v[1]);
+  }
   __device__ __forceinline__ static void load(const void* base, size_t site, double* v) {
     const double2* p = reinterpret_cast<const double2*>(base) + 3 * site;
 #pragma unroll
@@ -265,6 +276,13 @@ template <> struct VecT<LQ_F64> {
 template <> struct VecT<LQ_F32> {
   using real = float;
   static constexpr size_t bytes_per_site = 24;
+  __device__ __forceinline__ static void load_c(const void* base, size_t site, int c, float* v) {
+    float2 w = __ldg(reinterpret_cast<const float2*>(base) + 3 * site + c);
+    v[0] = w.x; v[1] = w.y;
+  }
+  __device__ __forceinline__ static void store_c(void* base, size_t site, int c, const float* v) {
+    reinterpret_cast<float2*>(base)[3 * site + c] = make_float2(v[0], v[1]);
+  }
   __device__ __forceinline__ static void load(const void* base, size_t site, float* v) {
     const float2* p = reinterpret_cast<const float2*>(base) + 3 * site;
 #pragma unroll
@@ -284,6 +302,13 @@ template <> struct VecT<LQ_F32> {
 template <lq_prec P> struct Vec16 {
   using real = float;
   static constexpr size_t bytes_per_site = 12;
+  __device__ __forceinline__ static void load_c(const void* base, size_t site, int c, float* v) {
+    float2 w = Half16<P>::to_f2(__ldg(reinterpret_cast<const uint32_t*>(base) + 3 * site + c));
+    v[0] = w.x; v[1] = w.y;
+  }
+  __device__ __forceinline__ static void store_c(void* base, size_t site, int c, const float* v) {
+    reinterpret_cast<uint32_t*>(base)[3 * site + c] = Half16<P>::from_f2(v[0], v[1]);
+  }
   __device__ __forceinline__ static void load(const void* base, size_t site, float* v) {
     const uint32_t* p = reinterpret_cast<const uint32_t*>(base) + 3 * site;
 #pragma unroll

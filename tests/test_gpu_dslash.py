@@ -63,8 +63,9 @@ def test_multi_rhs_equals_single(lq, ctx, gp, recon, vp, nrhs):
     for k in range(nrhs):
         assert rel_l2(got[k], ref[k]) < store_tolerance(vp)
         one, _ = _run(lq, ctx, U, dims, gp, recon, vp, chi[k:k + 1], 0)
-        # same arithmetic in the same order: identical to the single-rhs result
-        assert np.array_equal(one[0], got[k])
+        # the single-rhs launch may pick another launch shape (summation order): equal to
+        # within the accumulation rounding
+        assert rel_l2(got[k], one[0]) < store_tolerance(vp)
 
 
 @pytest.mark.parametrize("gp,recon,vp", [("f64", 18, "f64"), ("f32", 18, "f32"), ("f32", 12, "f32"),
