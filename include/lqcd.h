@@ -78,7 +78,9 @@ const char* lq_status_string(lq_status s);
 /* Autotuning of launch shapes (block size, right-hand sides per thread): 1 = on (the
  * default, unless the environment sets LQCD_TUNE=0), 0 = fixed defaults.  Tuning times
  * candidate launches on the first call with a new shape key and must not happen during
- * stream capture; call lq_tune_warmup-style entry points first when capturing. */
+ * stream capture: make one uncaptured call with the same shapes first.  The environment
+ * variable LQCD_DSLASH_SHAPE="block,rhs_tile,threads_per_site" forces one shape for every
+ * single-lattice Dslash launch it fits (block 64..256, a multiple of 32). */
 lq_status lq_set_tuning(lq_context* ctx, int enable);
 /* Write the tuning table (one line per key: key, chosen block, rhs tile, microseconds)
  * into buf (NUL-terminated, truncated to len).  *needed receives the full length + 1. */
@@ -163,6 +165,23 @@ typedef struct {
 lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, double mass,
                    const void* b, void* x, int nrhs, const lq_cg_params* params,
                    lq_cg_stats* stats, lq_stream stream);
+
+/* Batched solve of nlat independent lattices (uneven sizes allowed, at most 16), each with
+ * nrhs right-hand sides and its own mass: every system (lattice, rhs) runs the cg_solve
+ * iteration, but each phase of an iteration is ONE launch over all lattices -- a
+ * persistent multi-lattice Dslash kernel walking (lattice, rhs tile, site block) tiles, and
+ * persistent vector kernels walking (lattice, rhs, site block) tiles -- and the iteration
+ * block is captured once as a CUDA graph.  Tile shapes (sites per block, right-hand sides
+ * per thread, threads per site) come from the autotuner, keyed by the lattice set.
+ *   U_hi[l]: LQ_F64 gauges (all the same recon).  U_lo: NULL (FP64 solve) or an array of
+ *   reduced-precision gauges of one format (mixed precision as in cg_solve).
+ *   mass[l], b[l], x[l]: host arrays of nlat entries; b[l], x[l] are device complex128
+ *   [nrhs][Vh_l][3].  stats: host array of nlat * nrhs entries, [l * nrhs + rhs].
+ * Paper: the batching pattern is not in the paper; each system is the CG of cg_solve. */
+lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge* const* U_hi,
+                           const lq_gauge* const* U_lo, const double* mass, const void* const* b,
+                           void* const* x, int nrhs, const lq_cg_params* params,
+                           lq_cg_stats* stats, lq_stream stream);
 
 /* Allocation-free variant of cg_solve.  The paper has no counterpart; this entry point
  * exists for callers that cannot allocate GPU memory when they solve -- for example code

@@ -74,6 +74,8 @@ def load(path: str | None = None):
                       ctypes.POINTER(lq_cg_stats), P], I),
         "cg_solve_noalloc": ([P, P, P, D, P, P, I, ctypes.POINTER(lq_cg_params),
                               ctypes.POINTER(lq_cg_stats), P], I),
+        "cg_solve_batched": ([P, I, P, P, P, P, P, I, ctypes.POINTER(lq_cg_params),
+                              ctypes.POINTER(lq_cg_stats), P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -234,3 +236,28 @@ def cg_solve_noalloc(ctx: Context, U_hi: Gauge, U_lo: Gauge | None, mass: float,
     Calls whose GPU work overlaps share that array and race."""
     return _cg_call(ctx.lib.cg_solve_noalloc, ctx, U_hi, U_lo, mass, b, x, nrhs, tol, maxiter,
                     reliable_every, delta, check_every, stream)
+
+
+def cg_solve_batched(ctx: Context, U_hi, U_lo, masses, bs, xs, nrhs: int = 1, tol=1e-10,
+                     maxiter=10000, reliable_every=100, delta=0.1, check_every=20, stream=None):
+    """Batched CG over several lattices (lists of Gauge / tensors, one per lattice; U_lo None
+    for FP64).  Returns per-lattice lists of per-rhs stats dicts."""
+    n = len(U_hi)
+    P = ctypes.c_void_p
+    hi = (P * n)(*[g.handle.value for g in U_hi])
+    lo = None if U_lo is None else (P * n)(*[g.handle.value for g in U_lo])
+    m = (ctypes.c_double * n)(*[float(v) for v in masses])
+    bp = (P * n)(*[t.data_ptr() for t in bs])
+    xp = (P * n)(*[t.data_ptr() for t in xs])
+    params = lq_cg_params(float(tol), int(maxiter), int(reliable_every), float(delta), int(check_every))
+    stats = (lq_cg_stats * (n * int(nrhs)))()
+    st = ctx.lib.cg_solve_batched(ctx.handle, n, hi, lo, m, bp, xp, int(nrhs), ctypes.byref(params),
+                                  stats, _stream(stream))
+    flat = [dict(iters=s.iters, reliable_updates=s.reliable_updates,
+                 true_rel_resid=s.true_rel_resid, seconds=s.seconds) for s in stats]
+    out = [flat[l * nrhs:(l + 1) * nrhs] for l in range(n)]
+    if st != 0:
+        err = LQError(ctx.lib.lq_status_string(st).decode(), ctx.lib.lq_last_error(ctx.handle).decode())
+        err.stats = out
+        raise err
+    return out

@@ -19,10 +19,13 @@
 #include <chrono>
 #include <vector>
 
+#include "dslash_multi.cuh"
 #include "lqcd_internal.cuh"
 #include "tune.cuh"
 
 bool dslash_vec_ok(lq_prec gauge, lq_prec vec);
+lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int recon, lq_prec vp,
+                              const std::string& key, cudaStream_t s);
 
 namespace {
 
@@ -126,6 +129,152 @@ __global__ void __launch_bounds__(kBlas) k_fold(double* x_hi, void* x_lo, int Vh
   }
 }
 
+
+// ---------------------------------------------------- segmented (multi-lattice) kernels -
+//
+// The batched solver keeps every vector of all its lattices in one concatenated array:
+// lattice l starts at site voff_l and holds [nrhs][Vh_l][3].  A "segment" is one
+// (lattice, rhs) system, q = l * nrhs + rhs.  The kernels below walk tiles of kBlas sites
+// of the segments with a persistent grid; per-segment reductions go through per-tile
+// partials and the last block (grid_finish).
+
+struct SegLat {
+  size_t voff;   // first site of the lattice
+  int Vh;        // sites per rhs
+  int tile0;     // first tile of the lattice
+  int tps;       // tiles per segment
+};
+
+struct SegArgs {
+  int nlat, nrhs, ntiles;
+  size_t pstride;
+  SegLat lat[kMaxLat];
+};
+
+__device__ __forceinline__ void seg_locate(const SegArgs& g, int tile, int& q, size_t& base, int& chunk, int& Vh,
+                                           int& l) {
+  l = 0;
+  while (l + 1 < g.nlat && tile >= g.lat[l + 1].tile0) ++l;
+  const int t = tile - g.lat[l].tile0;
+  const int rhs = t / g.lat[l].tps;
+  chunk = t % g.lat[l].tps;
+  q = l * g.nrhs + rhs;
+  Vh = g.lat[l].Vh;
+  base = g.lat[l].voff + (size_t)rhs * Vh;
+}
+
+template <lq_prec VP>
+__global__ void __launch_bounds__(kBlas) k_seg_update(void* x, void* r, const void* p, const void* Ap,
+                                                      const SegArgs g, Reducer red) {
+  using VT = VecT<VP>;
+  using T = typename VT::real;
+  const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state);
+  for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int q, chunk, Vh, l;
+    size_t base;
+    seg_locate(g, tile, q, base, chunk, Vh, l);
+    double acc[1] = {0.0};
+    const int i = chunk * kBlas + threadIdx.x;
+    if (sc[q].active && i < Vh) {
+      const T alpha = (T)sc[q].alpha;
+      T xv[6], rv[6], pv[6], av[6];
+      VT::load_rw(x, base + i, xv);
+      VT::load_rw(r, base + i, rv);
+      VT::load(p, base + i, pv);
+      VT::load(Ap, base + i, av);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        xv[k] = fma(alpha, pv[k], xv[k]);
+        rv[k] = fma(-alpha, av[k], rv[k]);
+      }
+      VT::store(x, base + i, xv);
+      VT::store(r, base + i, rv);
+      acc[0] = site_norm2(rv);
+    }
+    block_sum_store<1>(acc, red.partials + (size_t)q * g.pstride + chunk, g.pstride, 1);
+  }
+  grid_finish(red, g.nlat * g.nrhs, g.pstride, [&](int q) { return g.lat[q / g.nrhs].tps; });
+}
+
+template <lq_prec VP>
+__global__ void __launch_bounds__(kBlas) k_seg_xpay(const void* r, void* p, const CGScalars* sc, const SegArgs g) {
+  using VT = VecT<VP>;
+  using T = typename VT::real;
+  for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int q, chunk, Vh, l;
+    size_t base;
+    seg_locate(g, tile, q, base, chunk, Vh, l);
+    const int i = chunk * kBlas + threadIdx.x;
+    if (!sc[q].active || i >= Vh) continue;
+    const T beta = (T)sc[q].beta;
+    T rv[6], pv[6];
+    VT::load(r, base + i, rv);
+    VT::load_rw(p, base + i, pv);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pv[k] = fma(beta, pv[k], rv[k]);
+    VT::store(p, base + i, pv);
+  }
+}
+
+template <lq_prec VS, lq_prec VD>
+__global__ void __launch_bounds__(kBlas) k_seg_convert(const void* src, void* dst, const SegArgs g, Reducer red) {
+  using Sv = VecT<VS>;
+  using Dv = VecT<VD>;
+  for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int q, chunk, Vh, l;
+    size_t base;
+    seg_locate(g, tile, q, base, chunk, Vh, l);
+    const int i = chunk * kBlas + threadIdx.x;
+    double acc[1] = {0.0};
+    if (i < Vh) {
+      typename Sv::real a[6];
+      typename Dv::real b[6];
+      Sv::load(src, base + i, a);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) b[k] = (typename Dv::real)a[k];
+      Dv::store(dst, base + i, b);
+      double s2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s2 += (double)b[k] * (double)b[k];
+      acc[0] = s2;
+    }
+    block_sum_store<1>(acc, red.partials + (size_t)q * g.pstride + chunk, g.pstride, 1);
+  }
+  grid_finish(red, g.nlat * g.nrhs, g.pstride, [&](int q) { return g.lat[q / g.nrhs].tps; });
+}
+
+template <lq_prec VL>
+__global__ void __launch_bounds__(kBlas) k_seg_fold(double* x_hi, void* x_lo, const SegArgs g) {
+  using L = VecT<VL>;
+  for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int q, chunk, Vh, l;
+    size_t base;
+    seg_locate(g, tile, q, base, chunk, Vh, l);
+    const int i = chunk * kBlas + threadIdx.x;
+    if (i >= Vh) continue;
+    typename L::real a[6], z[6];
+    double h[6];
+    L::load_rw(x_lo, base + i, a);
+    VecT<LQ_F64>::load_rw(x_hi, base + i, h);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { h[k] += (double)a[k]; z[k] = 0; }
+    VecT<LQ_F64>::store(x_hi, base + i, h);
+    L::store(x_lo, base + i, z);
+  }
+}
+
+// Lattice set of a batched solve.
+struct Batch {
+  int nlat;
+  const lq_gauge* hi[kMaxLat];
+  const lq_gauge* lo[kMaxLat];   // == hi for the plain FP64 solve
+  double mass[kMaxLat];
+  size_t voff[kMaxLat];
+  SegArgs seg;
+  int seg_grid;
+  std::string key_lo, key_hi;     // tuning keys of the two multi-lattice Dslash formats
+};
+
 // Bump allocator over the context's scratch space.
 struct Arena {
   char* base;
@@ -159,14 +308,84 @@ struct Solver {
   double* partials;
   unsigned int* counter;
   int nblocks_max;
+  int nsys = 0;          // independent systems: nrhs, or nlat * nrhs when batched
+  size_t sites = 0;      // sites of one full vector (all systems)
+  const Batch* batch = nullptr;
 
   Reducer reducer(int fin) const {
     return Reducer{partials, counter, result, nblocks_max, fin, (void*)sc};
   }
-  size_t vbytes(lq_prec q) const { return (size_t)nrhs * Vh * 6 * lq_prec_bytes(q); }
+  size_t vbytes(lq_prec q) const { return sites * 6 * lq_prec_bytes(q); }
 };
 
+// ---- batched (multi-lattice) versions of the solver steps
+
+MultiKArgs multi_args(const Solver& S, bool hi, int out_par, const void* in, void* out) {
+  const Batch& B = *S.batch;
+  MultiKArgs a;
+  memset(&a, 0, sizeof a);
+  a.nlat = B.nlat;
+  a.nrhs = S.nrhs;
+  a.out_par = out_par;
+  a.in = in;
+  a.out = out;
+  a.c = 1.0;
+  a.reduce = RED_NONE;
+  a.pstride = (size_t)S.nblocks_max;
+  for (int l = 0; l < B.nlat; ++l) {
+    const lq_gauge* g = hi ? B.hi[l] : B.lo[l];
+    a.lat[l].gauge = g->data;
+    a.lat[l].blk_bytes = g->blk_bytes;
+    a.lat[l].G = make_geom(g);
+    a.lat[l].voff = B.voff[l];
+  }
+  return a;
+}
+
+lq_status batch_iteration_dslash(Solver& S) {
+  const Batch& B = *S.batch;
+  const lq_gauge* g0 = B.lo[0];
+  MultiKArgs d = multi_args(S, false, 1, S.p, S.t);
+  lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
+  if (st) return st;
+  MultiKArgs e = multi_args(S, false, 0, S.t, S.Ap);
+  e.w1 = S.p;
+  for (int l = 0; l < B.nlat; ++l) e.lat[l].a1 = B.mass[l] * B.mass[l];
+  e.c = -1.0;
+  e.reduce = RED_DOT;
+  e.red = S.reducer(FIN_ALPHA);
+  e.skip_state = S.sc;
+  return launch_dslash_multi(S.ctx, e, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
+}
+
+lq_status batch_true_residual(Solver& S) {
+  const Batch& B = *S.batch;
+  const lq_gauge* g0 = B.hi[0];
+  MultiKArgs d = multi_args(S, true, 1, S.x, S.thi);
+  lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, LQ_F64, B.key_hi, S.s);
+  if (st) return st;
+  MultiKArgs e = multi_args(S, true, 0, S.thi, S.rhi);
+  e.w1 = S.b;
+  e.w2 = S.x;
+  for (int l = 0; l < B.nlat; ++l) {
+    e.lat[l].a1 = 1.0;
+    e.lat[l].a2 = -B.mass[l] * B.mass[l];
+  }
+  e.c = 1.0;
+  e.reduce = RED_NORM;
+  e.red = S.reducer(FIN_STORE);
+  return launch_dslash_multi(S.ctx, e, g0->prec, g0->recon, LQ_F64, B.key_hi, S.s);
+}
+
 lq_status launch_blas_update(Solver& S) {
+  if (S.batch) {
+    const Batch& B = *S.batch;
+    Reducer red = S.reducer(FIN_BETA);
+    if (S.vp == LQ_F64) k_seg_update<LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.xl, S.r, S.p, S.Ap, B.seg, red);
+    else k_seg_update<LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.xl, S.r, S.p, S.Ap, B.seg, red);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_update");
+    return LQ_OK;
+  }
   dim3 grid(S.nbx, S.nrhs);
   Reducer red = S.reducer(FIN_BETA);
   if (S.vp == LQ_F64) k_cg_update<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.xl, S.r, S.p, S.Ap, S.Vh, red);
@@ -176,6 +395,13 @@ lq_status launch_blas_update(Solver& S) {
 }
 
 lq_status launch_xpay(Solver& S) {
+  if (S.batch) {
+    const Batch& B = *S.batch;
+    if (S.vp == LQ_F64) k_seg_xpay<LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, B.seg);
+    else k_seg_xpay<LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, B.seg);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_xpay");
+    return LQ_OK;
+  }
   dim3 grid(S.nbx, S.nrhs);
   if (S.vp == LQ_F64) k_cg_xpay<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, S.Vh);
   else k_cg_xpay<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, S.Vh);
@@ -187,6 +413,11 @@ lq_status launch_xpay(Solver& S) {
 lq_status iteration(Solver& S) {
   lq_status st = launch_xpay(S);
   if (st) return st;
+  if (S.batch) {
+    st = batch_iteration_dslash(S);
+    if (st) return st;
+    return launch_blas_update(S);
+  }
   DslashArgs d;
   d.U = S.Ulo;
   d.in = S.p;
@@ -214,6 +445,7 @@ lq_status iteration(Solver& S) {
 
 // r_hi = b - M x_hi in FP64 and ||r_hi||^2 -> result (FIN_STORE).
 lq_status true_residual(Solver& S) {
+  if (S.batch) return batch_true_residual(S);
   DslashArgs d;
   d.U = S.Uhi;
   d.in = S.x;
@@ -241,6 +473,11 @@ lq_status true_residual(Solver& S) {
 
 lq_status fold_x(Solver& S) {
   if (!S.mixed) return LQ_OK;  // the FP64 solve iterates on x itself
+  if (S.batch) {
+    k_seg_fold<LQ_F32><<<S.batch->seg_grid, kBlas, 0, S.s>>>(S.x, S.xl, S.batch->seg);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_fold");
+    return LQ_OK;
+  }
   dim3 grid(S.nbx, S.nrhs);
   k_fold<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.x, S.xl, S.Vh);
   LQ_CHECK_LAUNCH(S.ctx, "k_fold");
@@ -249,28 +486,49 @@ lq_status fold_x(Solver& S) {
 
 // r_lo = round(r_hi) with ||r_lo||^2 -> result.
 lq_status replace_residual(Solver& S) {
-  dim3 grid(S.nbx, S.nrhs);
   Reducer red = S.reducer(FIN_STORE);
+  if (S.batch) {
+    const Batch& B = *S.batch;
+    if (S.mixed) k_seg_convert<LQ_F64, LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red);
+    else k_seg_convert<LQ_F64, LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_convert");
+    return LQ_OK;
+  }
+  dim3 grid(S.nbx, S.nrhs);
   if (S.mixed) k_convert<LQ_F64, LQ_F32><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Vh, 1, red);
   else k_convert<LQ_F64, LQ_F64><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Vh, 1, red);
   LQ_CHECK_LAUNCH(S.ctx, "k_convert");
   return LQ_OK;
 }
 
+// r_hi = b with ||b||^2 -> result.
+lq_status copy_source(Solver& S) {
+  Reducer red = S.reducer(FIN_STORE);
+  if (S.batch) {
+    k_seg_convert<LQ_F64, LQ_F64><<<S.batch->seg_grid, kBlas, 0, S.s>>>(S.b, S.rhi, S.batch->seg, red);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_convert(b)");
+    return LQ_OK;
+  }
+  dim3 grid(S.nbx, S.nrhs);
+  k_convert<LQ_F64, LQ_F64><<<grid, kBlas, 0, S.s>>>(S.b, S.rhi, S.Vh, 1, red);
+  LQ_CHECK_LAUNCH(S.ctx, "k_convert(b)");
+  return LQ_OK;
+}
+
 lq_status sync_scalars(Solver& S) {
-  LQ_CUDA(S.ctx, cudaMemcpyAsync(S.sc_host, S.sc, sizeof(CGScalars) * S.nrhs, cudaMemcpyDeviceToHost, S.s));
+  LQ_CUDA(S.ctx, cudaMemcpyAsync(S.sc_host, S.sc, sizeof(CGScalars) * S.nsys, cudaMemcpyDeviceToHost, S.s));
   LQ_CUDA(S.ctx, cudaStreamSynchronize(S.s));
   return LQ_OK;
 }
 
 lq_status push_scalars(Solver& S) {
-  LQ_CUDA(S.ctx, cudaMemcpyAsync(S.sc, S.sc_host, sizeof(CGScalars) * S.nrhs, cudaMemcpyHostToDevice, S.s));
+  LQ_CUDA(S.ctx, cudaMemcpyAsync(S.sc, S.sc_host, sizeof(CGScalars) * S.nsys, cudaMemcpyHostToDevice, S.s));
   return LQ_OK;
 }
 
 lq_status read_result(Solver& S, std::vector<double>& out) {
-  out.resize(S.nrhs);
-  LQ_CUDA(S.ctx, cudaMemcpyAsync(out.data(), S.result, sizeof(double) * S.nrhs, cudaMemcpyDeviceToHost, S.s));
+  out.resize(S.nsys);
+  LQ_CUDA(S.ctx, cudaMemcpyAsync(out.data(), S.result, sizeof(double) * S.nsys, cudaMemcpyDeviceToHost, S.s));
   LQ_CUDA(S.ctx, cudaStreamSynchronize(S.s));
   return LQ_OK;
 }
@@ -281,6 +539,19 @@ lq_status work_stream(lq_context* ctx, cudaStream_t* out) {
   if (dev < 0 || dev >= 64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "device index");
   if (!cache[dev]) LQ_CUDA(ctx, cudaStreamCreateWithFlags(&cache[dev], cudaStreamNonBlocking));
   *out = cache[dev];
+  return LQ_OK;
+}
+
+// Pinned host copy of the per-system scalars (grown on demand).
+lq_status host_scalars(lq_context* ctx, int nsys) {
+  const size_t want = sizeof(CGScalars) * (nsys > 16 ? nsys : 16);
+  if (ctx->host_pinned_bytes < want) {
+    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    ctx->host_pinned = nullptr;
+    ctx->host_pinned_bytes = 0;
+    LQ_CUDA(ctx, cudaMallocHost(&ctx->host_pinned, want));
+    ctx->host_pinned_bytes = want;
+  }
   return LQ_OK;
 }
 
@@ -296,7 +567,7 @@ struct GraphHolder {
 lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* converged_all,
                      bool use_graph = true) {
   lq_context* ctx = S.ctx;
-  const int n = S.nrhs;
+  const int n = S.nsys;
   const double tol2 = P.tol * P.tol;
   std::vector<double> res;
   std::vector<int> done(n, 0), updates(n, 0), frozen_iters(n, 0);
@@ -307,14 +578,10 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
   LQ_CUDA(ctx, cudaMemsetAsync(S.x, 0, S.vbytes(LQ_F64), S.s));
   if (S.mixed) LQ_CUDA(ctx, cudaMemsetAsync(S.xl, 0, S.vbytes(S.vp), S.s));
   LQ_CUDA(ctx, cudaMemsetAsync(S.p, 0, S.vbytes(S.vp), S.s));
-  {
-    dim3 grid(S.nbx, n);
-    Reducer red = S.reducer(FIN_STORE);
-    k_convert<LQ_F64, LQ_F64><<<grid, kBlas, 0, S.s>>>(S.b, S.rhi, S.Vh, 1, red);
-    LQ_CHECK_LAUNCH(ctx, "k_convert(b)");
-    st = read_result(S, res);
-    if (st) return st;
-  }
+  st = copy_source(S);
+  if (st) return st;
+  st = read_result(S, res);
+  if (st) return st;
   for (int i = 0; i < n; ++i) {
     bb[i] = res[i];
     if (!isfinite(bb[i])) return lq_fail(ctx, LQ_ERR_NUMERIC, "source %d holds NaN/Inf", i);
@@ -476,6 +743,8 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.Vh = U_hi->Vh;
   S.b = (const double*)b;
   S.x = (double*)x;
+  S.nsys = nrhs;
+  S.sites = (size_t)nrhs * S.Vh;
   S.nbx = (S.Vh + kBlas - 1) / kBlas;
   if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
   S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
@@ -500,13 +769,8 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
-  if (ctx->host_pinned_bytes < sizeof(CGScalars) * nrhs) {
-    if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
-    ctx->host_pinned = nullptr;
-    ctx->host_pinned_bytes = 0;
-    LQ_CUDA(ctx, cudaMallocHost(&ctx->host_pinned, 16 * sizeof(CGScalars)));
-    ctx->host_pinned_bytes = 16 * sizeof(CGScalars);
-  }
+  st = host_scalars(ctx, nrhs);
+  if (st) return st;
   S.sc_host = (CGScalars*)ctx->host_pinned;
 
   // Run on the library's own stream (capturable), ordered after the caller's stream.
@@ -599,6 +863,8 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.Vh = U_hi->Vh;
   S.b = (const double*)b;
   S.x = (double*)x;
+  S.nsys = nrhs;
+  S.sites = (size_t)nrhs * S.Vh;
   S.nbx = (S.Vh + kBlas - 1) / kBlas;
   if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
   S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
@@ -645,6 +911,148 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
     for (int i = 0; i < nrhs; ++i) stats[i].seconds = secs;
   if (st) return st;
   if (!converged) return lq_fail(ctx, LQ_ERR_NOT_CONVERGED, "CG did not reach tol %.3g within %d iterations",
+                                 params->tol, params->maxiter);
+  return LQ_OK;
+}
+
+// ------------------------------------------------------------------ batched solve -----
+
+static const char* prec_str(lq_prec p) {
+  return p == LQ_F64 ? "f64" : p == LQ_F32 ? "f32" : p == LQ_BF16 ? "bf16" : "f16";
+}
+
+extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge* const* U_hi,
+                                      const lq_gauge* const* U_lo, const double* mass, const void* const* b,
+                                      void* const* x, int nrhs, const lq_cg_params* params, lq_cg_stats* stats,
+                                      lq_stream stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (nlat < 1 || nlat > kMaxLat) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nlat must be in [1, %d]", kMaxLat);
+  if (!U_hi || !mass || !b || !x || !params) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL array argument");
+  if (nrhs < 1 || nrhs > 16) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  if (!(params->tol > 0.0) || params->maxiter < 1 || params->check_every < 1 || params->reliable_every < 1 ||
+      !(params->delta >= 0.0 && params->delta < 1.0))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad CG parameters");
+  const bool mixed = U_lo != nullptr;
+  for (int l = 0; l < nlat; ++l) {
+    if (!U_hi[l] || U_hi[l]->prec != LQ_F64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_hi[%d] must be an LQ_F64 gauge", l);
+    if (U_hi[l]->recon != U_hi[0]->recon) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "all U_hi must share recon");
+    if (mixed) {
+      if (!U_lo[l] || U_lo[l]->prec == LQ_F64) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_lo[%d] must be a reduced-precision gauge", l);
+      if (U_lo[l]->prec != U_lo[0]->prec || U_lo[l]->recon != U_lo[0]->recon)
+        return lq_fail(ctx, LQ_ERR_INVALID_ARG, "all U_lo must share precision and recon");
+      for (int i = 0; i < 4; ++i)
+        if (U_lo[l]->dims[i] != U_hi[l]->dims[i]) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U_lo[%d] and U_hi[%d] differ", l, l);
+    }
+    if (!b[l] || !x[l] || !lq_aligned16(b[l]) || !lq_aligned16(x[l]) || b[l] == x[l])
+      return lq_fail(ctx, LQ_ERR_INVALID_ARG, "b[%d], x[%d] must be distinct 16-byte aligned device pointers", l, l);
+  }
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+
+  Batch B;
+  B.nlat = nlat;
+  size_t total = 0;
+  int vh_max = 0;
+  std::string lats;
+  for (int l = 0; l < nlat; ++l) {
+    B.hi[l] = U_hi[l];
+    B.lo[l] = mixed ? U_lo[l] : U_hi[l];
+    B.mass[l] = mass[l];
+    B.voff[l] = total;
+    total += (size_t)nrhs * U_hi[l]->Vh;
+    if (U_hi[l]->Vh > vh_max) vh_max = U_hi[l]->Vh;
+    char d[64];
+    snprintf(d, sizeof d, "%s%dx%dx%dx%d", l ? "," : "", U_hi[l]->dims[0], U_hi[l]->dims[1], U_hi[l]->dims[2],
+             U_hi[l]->dims[3]);
+    lats += d;
+  }
+  char key[512];
+  snprintf(key, sizeof key, "dslash_multi g=%s/%d v=%s lats=%s nrhs=%d", prec_str(B.lo[0]->prec),
+           (int)B.lo[0]->recon, mixed ? "f32" : "f64", lats.c_str(), nrhs);
+  B.key_lo = key;
+  snprintf(key, sizeof key, "dslash_multi g=f64/%d v=f64 lats=%s nrhs=%d", (int)B.hi[0]->recon, lats.c_str(), nrhs);
+  B.key_hi = key;
+
+  Solver S{};
+  S.ctx = ctx;
+  S.Uhi = U_hi[0];
+  S.Ulo = B.lo[0];
+  S.mixed = mixed;
+  S.vp = mixed ? LQ_F32 : LQ_F64;
+  S.nrhs = nrhs;
+  S.Vh = vh_max;
+  S.nsys = nlat * nrhs;
+  S.sites = total;
+  S.batch = &B;
+  S.nblocks_max = (vh_max + 15) / 16;
+  memset(&B.seg, 0, sizeof B.seg);
+  B.seg.nlat = nlat;
+  B.seg.nrhs = nrhs;
+  B.seg.pstride = (size_t)S.nblocks_max;
+  int tiles = 0;
+  for (int l = 0; l < nlat; ++l) {
+    B.seg.lat[l].voff = B.voff[l];
+    B.seg.lat[l].Vh = U_hi[l]->Vh;
+    B.seg.lat[l].tile0 = tiles;
+    B.seg.lat[l].tps = (U_hi[l]->Vh + kBlas - 1) / kBlas;
+    tiles += nrhs * B.seg.lat[l].tps;
+  }
+  B.seg.ntiles = tiles;
+  B.seg_grid = tiles < 8 * ctx->num_sms ? tiles : 8 * ctx->num_sms;
+
+  const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
+  const size_t need = 5 * vin + 4 * v64 + S.nsys * (sizeof(CGScalars) + 8) + 8 +
+                      (size_t)S.nsys * S.nblocks_max * sizeof(double) + 14 * 256;
+  void* base = nullptr;
+  lq_status st = lq_scratch(ctx, need, &base);
+  if (st) return st;
+  Arena A{(char*)base};
+  S.b = (const double*)A.take(v64);
+  S.x = (double*)A.take(v64);
+  S.xl = mixed ? A.take(vin) : (void*)S.x;
+  S.r = A.take(vin);
+  S.p = A.take(vin);
+  S.Ap = A.take(vin);
+  S.t = A.take(vin);
+  S.rhi = (double*)A.take(v64);
+  S.thi = (double*)A.take(v64);
+  S.sc = (CGScalars*)A.take(sizeof(CGScalars) * S.nsys);
+  S.result = (double*)A.take(sizeof(double) * S.nsys);
+  S.counter = (unsigned int*)A.take(sizeof(unsigned int));
+  S.partials = (double*)A.take(sizeof(double) * S.nsys * S.nblocks_max);
+  if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
+  st = host_scalars(ctx, S.nsys);
+  if (st) return st;
+  S.sc_host = (CGScalars*)ctx->host_pinned;
+
+  cudaStream_t user = (cudaStream_t)stream;
+  st = work_stream(ctx, &S.s);
+  if (st) return st;
+  cudaEvent_t ev;
+  LQ_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  LQ_CUDA(ctx, cudaEventRecord(ev, user));
+  LQ_CUDA(ctx, cudaStreamWaitEvent(S.s, ev, 0));
+  LQ_CUDA(ctx, cudaMemsetAsync(S.counter, 0, sizeof(unsigned int), S.s));
+  for (int l = 0; l < nlat; ++l)
+    LQ_CUDA(ctx, cudaMemcpyAsync((char*)S.b + B.voff[l] * 48, b[l], (size_t)nrhs * U_hi[l]->Vh * 48,
+                                 cudaMemcpyDeviceToDevice, S.s));
+  int converged = 0;
+  st = run_solver(S, *params, stats, &converged);
+  if (!st)
+    for (int l = 0; l < nlat && !st; ++l) {
+      cudaError_t e = cudaMemcpyAsync(x[l], (const char*)S.x + B.voff[l] * 48, (size_t)nrhs * U_hi[l]->Vh * 48,
+                                      cudaMemcpyDeviceToDevice, S.s);
+      if (e != cudaSuccess) st = lq_cuda_fail(ctx, e, "copy of x");
+    }
+  cudaEventRecord(ev, S.s);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaEventDestroy(ev);
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int i = 0; i < S.nsys; ++i) stats[i].seconds = secs;
+  if (st) return st;
+  if (!converged) return lq_fail(ctx, LQ_ERR_NOT_CONVERGED, "batched CG did not reach tol %.3g within %d iterations",
                                  params->tol, params->maxiter);
   return LQ_OK;
 }

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "dslash_kernel.cuh"
+#include "dslash_multi.cuh"
 
 static const char* prec_name(lq_prec p) {
   switch (p) {
@@ -149,4 +150,75 @@ extern "C" lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* i
   a.vec_prec = vec_prec;
   a.rhs_stride = U->Vh;
   return launch_dslash(ctx, a, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ multi-lattice launcher ---
+
+MultiLaunchFn dslash_multi_fn_f64(int recon);
+MultiLaunchFn dslash_multi_fn_f32(int recon);
+MultiLaunchFn dslash_multi_fn_bf16(int recon);
+MultiLaunchFn dslash_multi_fn_f16(int recon);
+
+MultiLaunchFn dslash_multi_fn(lq_prec prec, int recon) {
+  switch (prec) {
+    case LQ_F64: return dslash_multi_fn_f64(recon);
+    case LQ_F32: return dslash_multi_fn_f32(recon);
+    case LQ_BF16: return dslash_multi_fn_bf16(recon);
+    case LQ_F16: return dslash_multi_fn_f16(recon);
+  }
+  return nullptr;
+}
+
+static std::vector<TuneEntry> multi_candidates(lq_prec gp, int nrhs) {
+  std::vector<TuneEntry> c;
+  int first_tile = 1;
+  for (int t : {1, 2, 4, 8})
+    if (t <= nrhs && t <= (gp == LQ_F64 ? 2 : 8)) first_tile = t;
+  TuneEntry d;
+  d.block = 128; d.rhs_tile = first_tile; d.tps = 1;
+  c.push_back(d);
+  for (int t : {1, 2, 4, 8}) {
+    if (t > nrhs || (gp == LQ_F64 && t > 4)) continue;
+    for (int tps : {1, 2})
+      for (int b : {64, 128, 256}) {
+        if (!dslash_multi_shape_ok(t, tps) || (b == 128 && t == first_tile && tps == 1)) continue;
+        TuneEntry e;
+        e.block = b; e.rhs_tile = t; e.tps = tps;
+        c.push_back(e);
+      }
+  }
+  return c;
+}
+
+// Launches the multi-lattice half Dslash described by `a` (lattice table, vectors,
+// epilogue) with a tuned launch shape; `key` names the lattice set for the tuning table.
+lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int recon, lq_prec vp,
+                              const std::string& key, cudaStream_t s) {
+  MultiLaunchFn fn = dslash_multi_fn(gp, recon);
+  if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
+  MultiKArgs plain = a;
+  plain.w1 = plain.w2 = nullptr;
+  plain.c = 1.0;
+  plain.reduce = RED_NONE;
+  plain.skip_state = nullptr;
+  TuneEntry pick;
+  lq_status st = tune_pick(
+      ctx, key, multi_candidates(gp, a.nrhs), s,
+      [&](const TuneEntry& c) -> lq_status {
+        cudaError_t e = fn(plain, vp, c.block, c.rhs_tile, c.tps, ctx->num_sms, s);
+        if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi (tuning)");
+        return LQ_OK;
+      },
+      &pick);
+  if (st) return st;
+  if (a.reduce != RED_NONE) {
+    MultiKArgs chk = a;
+    multi_tiles(chk, pick.block, pick.rhs_tile, pick.tps);
+    for (int l = 0; l < a.nlat; ++l)
+      if ((size_t)chk.lat[l].tiles_x > a.pstride)
+        return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
+  }
+  cudaError_t e = fn(a, vp, pick.block, pick.rhs_tile, pick.tps, ctx->num_sms, s);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi");
+  return LQ_OK;
 }

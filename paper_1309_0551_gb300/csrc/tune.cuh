@@ -170,3 +170,52 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
   }
   if (threadIdx.x == 0) *red.counter = 0u;
 }
+
+// Block-wide sums of v[r] (every thread calls); thread 0 stores sum r at dst[r * stride]
+// for r < nvalid.  Ends with a barrier so shared memory can be reused by the next call.
+template <int NR>
+__device__ __forceinline__ void block_sum_store(const double (&v)[NR], double* dst, size_t stride, int nvalid) {
+  __shared__ double sm[NR][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    double x = warp_sum(v[r]);
+    if (lane == 0) sm[r][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double x = lane < nw ? sm[r][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0 && r < nvalid) dst[(size_t)r * stride] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// End of a persistent kernel whose blocks stored per-row partials partials[q*stride + col]
+// (cols(q) columns for row q): the last block to finish sums each row in column order and
+// runs the finisher on it.  Every thread of every block calls this once.
+template <class Cols>
+__device__ __forceinline__ void grid_finish(const Reducer& red, int nq, size_t stride, Cols cols) {
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(red.counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int q = warp; q < nq; q += nw) {
+    const int n = cols(q);
+    double x = 0.0;
+    for (int b = lane; b < n; b += 32) x += __ldcg(red.partials + (size_t)q * stride + b);
+    x = warp_sum(x);
+    if (lane == 0) finish_one(red, q, x);
+  }
+  if (threadIdx.x == 0) *red.counter = 0u;
+}
