@@ -166,6 +166,25 @@ lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, 
                    const void* b, void* x, int nrhs, const lq_cg_params* params,
                    lq_cg_stats* stats, lq_stream stream);
 
+/* ------------------------------------------------------------------- force ---------- */
+
+/* Gradients of the pseudofermion action S = Re chi^dag M chi = m^2 ||chi||^2 + ||D_oe chi||^2
+ * (M = m^2 - D_eo D_oe, chi on the even sites).  The paper lists the building blocks
+ * (Table 1: su3_projector for the outer products, mult_su3_na for U G^dag) but not the
+ * force itself; conventions are the library's:
+ *   psi = D_oe chi (recomputed on every call);
+ *   dSdchi = 2 M chi  -- the gradient with respect to (Re chi, Im chi), packed as complex;
+ *   dSdU[mu][lex] = G = 2 Z^dag with Z = eta_mu(y) chi(y+mu) psi(y)^dag for odd y and
+ *     Z = -eta_mu(y) psi(y+mu) chi(y)^dag for even y, so that dS = Re sum Tr(G^dag dU);
+ *   force_TA[mu][lex] = TA(U G^dag), TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6, so that
+ *     d/de S(exp(e X) U) = Tr(X F) for every traceless anti-Hermitian X.
+ *   U: 18-real gauge, LQ_F64 or LQ_F32; chi (device, [Vh][3]) and every output use the
+ *   same precision (complex128 or complex64).  dSdU and force_TA are canonical gauge-shaped
+ *   [4][V][3][3]; any of dSdU, force_TA, dSdchi, S may be NULL.  S (host) makes the call
+ *   synchronise the stream.  Cost per call: two half Dslash and one pass over the links. */
+lq_status dslash_force(lq_context* ctx, const lq_gauge* U, double mass, const void* chi,
+                       void* dSdU, void* force_TA, void* dSdchi, double* S, lq_stream stream);
+
 /* Batched solve of nlat independent lattices (uneven sizes allowed, at most 16), each with
  * nrhs right-hand sides and its own mass: every system (lattice, rhs) runs the cg_solve
  * iteration, but each phase of an iteration is ONE launch over all lattices -- a

@@ -64,3 +64,34 @@ def ta(A):
 def force_ta(U, G):
     """F = TA(U G^dag) per link."""
     return ta(mult_su3_na(U, G))
+
+
+def link_gradient_sites(U, chi, mass, dims, links):
+    """G = dS/dU at the chosen links only, ``links`` a list of (mu, lex); for lattices too
+    large for ``link_gradient``.  psi is evaluated only at the odd sites the links touch."""
+    from .dslash import dslash_eo_sites
+    dims = tuple(dims)
+    V = int(np.prod(dims))
+    U = np.asarray(U).reshape(4, V, 3, 3)
+    touched = sorted({s for _, s in links} | {geo.neighbour_lex(dims, s, mu, +1) for mu, s in links})
+    odd = [s for s in touched if sum(geo.site_coords(dims, s)) % 2 == 1]
+    cb_of_odd = {s: int(np.count_nonzero(geo.parity(dims).reshape(-1)[:s] == 1)) for s in odd}
+    psi = dict(zip(odd, dslash_eo_sites(U, chi, dims, 1, [cb_of_odd[s] for s in odd])))
+    chi_at = {}
+    par = geo.parity(dims).reshape(-1)
+    out = np.empty((len(links), 3, 3), dtype=np.complex128)
+    for n, (mu, s) in enumerate(links):
+        c = geo.site_coords(dims, s)
+        eta = (1, (-1) ** c[0], (-1) ** (c[0] + c[1]), (-1) ** (c[0] + c[1] + c[2]))[mu]
+        f = geo.neighbour_lex(dims, s, mu, +1)
+        if par[s] == 1:
+            e = f
+            if e not in chi_at:
+                chi_at[e] = chi[int(np.count_nonzero(par[:e] == 0))]
+            Z = eta * su3_projector(chi_at[e], psi[s])
+        else:
+            if s not in chi_at:
+                chi_at[s] = chi[int(np.count_nonzero(par[:s] == 0))]
+            Z = -eta * su3_projector(psi[f], chi_at[s])
+        out[n] = 2.0 * adj(Z)
+    return out

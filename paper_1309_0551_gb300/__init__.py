@@ -76,6 +76,7 @@ def load(path: str | None = None):
                               ctypes.POINTER(lq_cg_stats), P], I),
         "cg_solve_batched": ([P, I, P, P, P, P, P, I, ctypes.POINTER(lq_cg_params),
                               ctypes.POINTER(lq_cg_stats), P], I),
+        "dslash_force": ([P, P, D, P, P, P, P, ctypes.POINTER(D), P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -261,3 +262,14 @@ def cg_solve_batched(ctx: Context, U_hi, U_lo, masses, bs, xs, nrhs: int = 1, to
         err.stats = out
         raise err
     return out
+
+
+def dslash_force(ctx: Context, U: Gauge, mass: float, chi, dSdU=None, force_TA=None, dSdchi=None,
+                 want_S: bool = False, stream=None):
+    """Gradients of S = Re chi^dag (m^2 - D_eo D_oe) chi (see lqcd.h); returns S (float) when
+    want_S, else None.  Outputs are written into the given tensors."""
+    S = ctypes.c_double(0.0)
+    ctx.check(ctx.lib.dslash_force(ctx.handle, U.handle, float(mass), _ptr(chi), _ptr(dSdU),
+                                   _ptr(force_TA), _ptr(dSdchi), ctypes.byref(S) if want_S else None,
+                                   _stream(stream)))
+    return S.value if want_S else None

@@ -1,0 +1,205 @@
+// Fermion force of S = Re chi^dag (m^2 - D_eo D_oe) chi, chi on the even sites.
+//
+//   psi = D_oe chi                                   (half Dslash, ||psi||^2 fused)
+//   dS/dchi = 2 M chi = 2 m^2 chi - 2 D_eo psi        (half Dslash with fused epilogue
+//                                                     and Re<chi, 2 M chi> = 2 S)
+//   per link U_mu(y):  Z =  eta_mu(y) chi(y+mu) psi(y)^dag      (y odd)
+//                      Z = -eta_mu(y) psi(y+mu) chi(y)^dag      (y even)
+//   (su3_projector outer products of Table 1), G = dS/dU = 2 Z^dag, F = TA(U G^dag),
+//   TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6.
+// psi is recomputed from chi on every call rather than kept from a forward pass.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lqcd_internal.cuh"
+#include "tune.cuh"
+
+namespace {
+
+constexpr int kForceThreads = 128;
+
+// Complex helpers on (re, im) pairs.
+template <class T> struct C2 { T r, i; };
+template <class T> __device__ __forceinline__ C2<T> cmul_conj(C2<T> a, C2<T> b) {  // a * conj(b)
+  return {a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i};
+}
+
+template <lq_prec P>
+__global__ void __launch_bounds__(kForceThreads) k_force(const char* __restrict__ gauge, size_t blk_bytes, Geom G,
+                                                         const void* __restrict__ chi, const void* __restrict__ psi,
+                                                         void* __restrict__ dSdU, void* __restrict__ fta) {
+  using L = LinkT<P, 18>;
+  using VT = VecT<P>;
+  using T = typename L::real;
+  const int V = 2 * G.Vh;
+  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
+  if (lex >= V) return;
+  const int x = lex % G.Lx;
+  int rest = lex / G.Lx;
+  const int y = rest % G.Ly;
+  rest /= G.Ly;
+  const int z = rest % G.Lz;
+  const int t = rest / G.Lz;
+  const int par = (x + y + z + t) & 1;
+  const int cb = lex >> 1;
+  // neighbour y + mu
+  int c[4] = {x, y, z, t};
+  const int Ls[4] = {G.Lx, G.Ly, G.Lz, G.Lt};
+  c[mu] = (c[mu] + 1 == Ls[mu]) ? 0 : c[mu] + 1;
+  const int lexf = c[0] + G.Lx * (c[1] + G.Ly * (c[2] + G.Lz * c[3]));
+  const int cbf = lexf >> 1;
+  const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+  const T eta = (ephase & 1) ? T(-1) : T(1);
+  // a = left vector, b = right vector of the outer product Z = s * a b^dag
+  T a[6], b[6];
+  T s;
+  if (par) {  // y odd: chi(y+mu) psi(y)^dag
+    VT::load(chi, cbf, a);
+    VT::load(psi, cb, b);
+    s = eta;
+  } else {    // y even: -psi(y+mu) chi(y)^dag
+    VT::load(psi, cbf, a);
+    VT::load(chi, cb, b);
+    s = -eta;
+  }
+  T u[18];
+  L::load(gauge + (size_t)(2 * mu + par) * blk_bytes, G.S, cb, u);
+  // Z_ij = s a_i conj(b_j)
+  C2<T> Z[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C2<T> p = cmul_conj(C2<T>{a[2 * i], a[2 * i + 1]}, C2<T>{b[2 * j], b[2 * j + 1]});
+      Z[i][j] = {s * p.r, s * p.i};
+    }
+  const size_t link = (size_t)mu * V + lex;
+  if (dSdU) {
+    // G = 2 Z^dag: G_ij = 2 conj(Z_ji)
+    T g[18];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        g[2 * (3 * i + j)] = T(2) * Z[j][i].r;
+        g[2 * (3 * i + j) + 1] = -T(2) * Z[j][i].i;
+      }
+    T* out = reinterpret_cast<T*>(dSdU) + link * 18;
+#pragma unroll
+    for (int k = 0; k < 18; k += 2) {
+      if constexpr (sizeof(T) == 8) reinterpret_cast<double2*>(out)[k / 2] = make_double2(g[k], g[k + 1]);
+      else reinterpret_cast<float2*>(out)[k / 2] = make_float2(g[k], g[k + 1]);
+    }
+  }
+  if (fta) {
+    // A = U G^dag = 2 U Z
+    C2<T> A[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const T ur = u[2 * (3 * i + k)], ui = u[2 * (3 * i + k) + 1];
+          re = fma(ur, Z[k][j].r, re);
+          re = fma(-ui, Z[k][j].i, re);
+          im = fma(ur, Z[k][j].i, im);
+          im = fma(ui, Z[k][j].r, im);
+        }
+        A[i][j] = {T(2) * re, T(2) * im};
+      }
+    // TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6 * 1; Tr(A - A^dag) = 2i Im Tr A
+    const T trim = (A[0][0].i + A[1][1].i + A[2][2].i) / T(3);
+    T f[18];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        f[2 * (3 * i + j)] = T(0.5) * (A[i][j].r - A[j][i].r);
+        f[2 * (3 * i + j) + 1] = T(0.5) * (A[i][j].i + A[j][i].i) - (i == j ? trim : T(0));
+      }
+    T* out = reinterpret_cast<T*>(fta) + link * 18;
+#pragma unroll
+    for (int k = 0; k < 18; k += 2) {
+      if constexpr (sizeof(T) == 8) reinterpret_cast<double2*>(out)[k / 2] = make_double2(f[k], f[k + 1]);
+      else reinterpret_cast<float2*>(out)[k / 2] = make_float2(f[k], f[k + 1]);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" lq_status dslash_force(lq_context* ctx, const lq_gauge* U, double mass, const void* chi, void* dSdU,
+                                  void* force_TA, void* dSdchi, double* S, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (!U || !chi) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U and chi are required");
+  if (U->recon != LQ_RECON_18 || (U->prec != LQ_F64 && U->prec != LQ_F32))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "dslash_force needs an 18-real LQ_F64 or LQ_F32 gauge");
+  if (!lq_aligned16(chi) || (dSdU && !lq_aligned16(dSdU)) || (force_TA && !lq_aligned16(force_TA)) ||
+      (dSdchi && !lq_aligned16(dSdchi)))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+  DeviceGuard dg(ctx->device);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const lq_prec vp = U->prec;
+  const size_t es = lq_prec_bytes(vp);
+  const size_t vbytes = (size_t)U->Vh * 6 * es;
+  const int nblocks_max = (U->Vh + 15) / 16;
+  // scratch: psi, dS/dchi (when the caller passes none), 1 scalar, counter, partials
+  const size_t need = 2 * vbytes + 64 + (size_t)nblocks_max * sizeof(double) + 6 * 256;
+  void* base = nullptr;
+  lq_status st = lq_scratch(ctx, need, &base);
+  if (st) return st;
+  char* p = (char*)base;
+  auto take = [&](size_t n) { p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255); void* r = p; p += n; return r; };
+  void* psi = take(vbytes);
+  void* dchi = dSdchi ? dSdchi : take(vbytes);
+  double* result = (double*)take(16);
+  unsigned int* counter = (unsigned int*)take(sizeof(unsigned int));
+  double* partials = (double*)take((size_t)nblocks_max * sizeof(double));
+  LQ_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  Reducer red{partials, counter, result, nblocks_max, 0 /*FIN_STORE*/, nullptr};
+
+  // psi = D_oe chi
+  DslashArgs d;
+  d.U = U;
+  d.in = chi;
+  d.out = psi;
+  d.out_parity = 1;
+  d.nrhs = 1;
+  d.vec_prec = vp;
+  d.rhs_stride = U->Vh;
+  st = launch_dslash(ctx, d, s);
+  if (st) return st;
+  // dS/dchi = 2 m^2 chi - 2 D_eo psi, and Re<chi, dS/dchi> = 2 S
+  DslashArgs e = d;
+  e.in = psi;
+  e.out = dchi;
+  e.out_parity = 0;
+  e.w1 = chi;
+  e.a1 = 2.0 * mass * mass;
+  e.c = -2.0;
+  e.reduce = RED_DOT;
+  e.red = &red;
+  st = launch_dslash(ctx, e, s);
+  if (st) return st;
+  if (dSdU || force_TA) {
+    Geom G = make_geom(U);
+    const int V = 2 * U->Vh;
+    dim3 grid((V + kForceThreads - 1) / kForceThreads, 4);
+    if (vp == LQ_F64) k_force<LQ_F64><<<grid, kForceThreads, 0, s>>>(U->data, U->blk_bytes, G, chi, psi, dSdU, force_TA);
+    else k_force<LQ_F32><<<grid, kForceThreads, 0, s>>>(U->data, U->blk_bytes, G, chi, psi, dSdU, force_TA);
+    LQ_CHECK_LAUNCH(ctx, "k_force");
+  }
+  if (S) {
+    double two_s = 0.0;
+    LQ_CUDA(ctx, cudaMemcpyAsync(&two_s, result, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LQ_CUDA(ctx, cudaStreamSynchronize(s));
+    *S = 0.5 * two_s;
+  }
+  return LQ_OK;
+}

@@ -144,3 +144,13 @@ def test_force_ta_directional_derivatives(field):
             fd = _delta_psi2(Up, Um, chi) / (2 * h)
             an = np.trace(X @ F[mu, s]).real
             assert abs(fd - an) < 1e-7 * scale, (mu, s, fd, an)
+
+
+def test_link_gradient_sites_matches_full(field):
+    U, chi = field
+    G = force.link_gradient(U, chi, MASS, DIMS)
+    g = synth.rng(50)
+    links = [(int(g.integers(0, 4)), int(g.integers(0, synth.volume(DIMS)))) for _ in range(40)]
+    Gs = force.link_gradient_sites(U, chi, MASS, DIMS, links)
+    for (mu, s), Gl in zip(links, Gs):
+        assert np.abs(Gl - G[mu, s]).max() < 1e-13
