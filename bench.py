@@ -42,7 +42,9 @@ BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 # makes the figure stale and the bench reports null.
 NCU_TRAFFIC = {}
 KERNEL_SOURCES = ("paper_1309_0551_gb300/csrc/dslash_kernel.cuh",
-                  "paper_1309_0551_gb300/csrc/lqcd_internal.cuh")
+                  "paper_1309_0551_gb300/csrc/dslash_site.cuh",
+                  "paper_1309_0551_gb300/csrc/lqcd_internal.cuh",
+                  "paper_1309_0551_gb300/csrc/tune.cuh")
 
 
 def kernel_hash() -> str:
@@ -369,6 +371,80 @@ def run_cg(lq, ctx, torch):
     return res
 
 
+def run_batched(lq, ctx, torch):
+    """Lattices 8^4, 12^4, 16^4, 24^4, 8 Gaussian right-hand sides each, links exp(i 0.2 H),
+    m = 0.1, FP32 inner iteration (12-real links), tol 1e-8: one batched solve against the
+    four solves one after the other."""
+    import synth
+    dims_list = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (24, 24, 24, 24)]
+    his, los, bs = [], [], []
+    for i, d in enumerate(dims_list):
+        U = torch.from_numpy(synth.gauge_field(d, "near_identity", seed=5 + i, eps=0.2)).cuda()
+        his.append(lq.lq_gauge_pack(ctx, d, U, "f64", 18))
+        los.append(lq.lq_gauge_pack(ctx, d, U, "f32", 12))
+        bs.append(torch.from_numpy(synth.fermion_field(d, 8, seed=105 + i)).cuda())
+    xs = [torch.empty_like(b) for b in bs]
+    kw = dict(tol=1e-8, maxiter=20000)
+    lq.cg_solve_batched(ctx, his, los, [0.1] * 4, bs, xs, 8, **kw)      # tunes the shapes
+    for h, l, b, x in zip(his, los, bs, xs):
+        lq.cg_solve(ctx, h, l, 0.1, b, x, 8, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = lq.cg_solve_batched(ctx, his, los, [0.1] * 4, bs, xs, 8, **kw)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for h, l, b, x in zip(his, los, bs, xs):
+        lq.cg_solve(ctx, h, l, 0.1, b, x, 8, **kw)
+    torch.cuda.synchronize()
+    t_sep = time.perf_counter() - t0
+    tune = [l for l in ctx.tune_report().splitlines() if "dslash_multi" in l and "8x8x8x8,12x12" in l]
+    return {"workload": "8^4+12^4+16^4+24^4, 8 RHS each, eps 0.2, m 0.1, FP32 inner (12-real), tol 1e-8",
+            "batched_seconds": round(t_batch, 4), "separate_seconds": round(t_sep, 4),
+            "speedup": round(t_sep / t_batch, 3),
+            "max_iters": max(s["iters"] for lat in st for s in lat),
+            "max_true_rel_resid": max(s["true_rel_resid"] for lat in st for s in lat),
+            "autotuned_multi_dslash": tune}
+
+
+def run_force(lq, ctx, torch):
+    """32^3 x 64, Haar links, m = 0.05, Gaussian chi: dslash_force (psi, dS/dchi, G and the
+    TA force) in FP32 and FP64."""
+    import synth
+    dims, mass = (32, 32, 32, 64), 0.05
+    U = torch.from_numpy(synth.gauge_field(dims, "haar", seed=6)).cuda()
+    chi0 = torch.from_numpy(synth.fermion_field(dims, 1, seed=7)[0])
+    V = synth.volume(dims)
+    out = {"workload": "32^3x64 Haar, m 0.05: psi = D_oe chi, dS/dchi, dS/dU and TA(U G^dag)"}
+    peak, _ = measured_peak()
+    for prec, ct in (("f32", torch.complex64), ("f64", torch.complex128)):
+        g = lq.lq_gauge_pack(ctx, dims, U, prec, 18)
+        chi = chi0.to(ct).cuda()
+        dU = torch.empty(U.shape, dtype=ct, device="cuda")
+        F = torch.empty(U.shape, dtype=ct, device="cuda")
+        dchi = torch.empty_like(chi)
+        for _ in range(2):
+            lq.dslash_force(ctx, g, mass, chi, dSdU=dU, force_TA=F, dSdchi=dchi)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n = 5
+        for _ in range(n):
+            lq.dslash_force(ctx, g, mass, chi, dSdU=dU, force_TA=F, dSdchi=dchi)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        s = BYTES[prec]
+        # two half Dslash (site_bytes each over V/2 sites) + the link pass: read U and the two
+        # vectors, write G and F
+        nbytes = 2 * (V // 2) * site_bytes(prec, 18, prec) + 4 * V * 18 * s * 3 + 2 * (V // 2) * 6 * s
+        out[prec] = {"ms": round(ms, 3), "gbs": round(nbytes / ms / 1e6, 1),
+                     "frac": round(nbytes / ms / 1e6 / peak, 3), "bytes": nbytes}
+        del g, dU, F, dchi
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_1309_0551_gb300 as lq
@@ -431,6 +507,8 @@ def run_ours(args):
         extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream, args.streams)
     if rank == 0 and not args.no_cg:
         extra["cg"] = run_cg(lq, ctx, torch)
+        extra["batched"] = run_batched(lq, ctx, torch)
+        extra["force"] = run_force(lq, ctx, torch)
     line = {
         "metric": METRIC,
         "value": round(value, 1),

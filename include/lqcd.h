@@ -133,6 +133,18 @@ lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* 
 lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
                     int out_parity, int nrhs, lq_prec vec_prec, lq_stream stream);
 
+/* The half Dslash of dslash_eo applied to nlat lattices (at most 16, sizes may differ) in
+ * ONE persistent launch: the work is cut into (lattice, rhs tile, site block) tiles that a
+ * grid of about one wave of resident blocks walks in a fixed order, so that many small
+ * lattices, or several independent fields, fill the GPU together.  Tile shapes are
+ * autotuned per lattice set.
+ *   U[l]: gauges of one storage format; in[l], out[l]: device, [nrhs][Vh_l][3] vectors.
+ *   Precision pairs: LQ_F64 links with LQ_F64 vectors; LQ_F32/LQ_BF16/LQ_F16 links with
+ *   LQ_F32 vectors. */
+lq_status dslash_eo_multi(lq_context* ctx, int nlat, const lq_gauge* const* U, const void* const* in,
+                          void* const* out, int out_parity, int nrhs, lq_prec vec_prec,
+                          lq_stream stream);
+
 /* ---------------------------------------------------------------------- CG ---------- */
 
 typedef struct {

@@ -77,6 +77,7 @@ def load(path: str | None = None):
         "cg_solve_batched": ([P, I, P, P, P, P, P, I, ctypes.POINTER(lq_cg_params),
                               ctypes.POINTER(lq_cg_stats), P], I),
         "dslash_force": ([P, P, D, P, P, P, P, ctypes.POINTER(D), P], I),
+        "dslash_eo_multi": ([P, I, P, P, P, I, I, I, P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -188,6 +189,18 @@ def dslash_eo(ctx: Context, U: Gauge, inp, out, out_parity: int, nrhs: int = 1, 
     vp = vec_prec_of(inp) if vec_prec is None else vec_prec
     ctx.check(ctx.lib.dslash_eo(ctx.handle, U.handle, _ptr(inp), _ptr(out), int(out_parity),
                                 int(nrhs), int(vp), _stream(stream)))
+
+
+def dslash_eo_multi(ctx: Context, Us, ins, outs, out_parity: int, nrhs: int = 1, vec_prec=None,
+                    stream=None):
+    """The half Dslash on several lattices in one persistent launch (lists, one per lattice)."""
+    n = len(Us)
+    P = ctypes.c_void_p
+    vp = vec_prec_of(ins[0]) if vec_prec is None else vec_prec
+    ctx.check(ctx.lib.dslash_eo_multi(ctx.handle, n, (P * n)(*[g.handle.value for g in Us]),
+                                      (P * n)(*[t.data_ptr() for t in ins]),
+                                      (P * n)(*[t.data_ptr() for t in outs]), int(out_parity), int(nrhs),
+                                      int(vp), _stream(stream)))
 
 
 def su3_mul_batch(ctx: Context, A, B, C, n=None, adjA=0, adjB=0, prec=None, stream=None):

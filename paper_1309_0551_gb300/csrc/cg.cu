@@ -320,24 +320,30 @@ struct Solver {
 
 // ---- batched (multi-lattice) versions of the solver steps
 
-MultiKArgs multi_args(const Solver& S, bool hi, int out_par, const void* in, void* out) {
+// Multi-lattice launch arguments over the concatenated vectors (lattice l at site offset
+// voff_l); w1, w2 may be NULL.
+MultiKArgs multi_args(const Solver& S, bool hi, int out_par, const void* in, void* out, const void* w1 = nullptr,
+                      const void* w2 = nullptr) {
   const Batch& B = *S.batch;
+  const size_t bps = hi || !S.mixed ? 48 : 24;  // bytes per site of the vectors
   MultiKArgs a;
   memset(&a, 0, sizeof a);
   a.nlat = B.nlat;
   a.nrhs = S.nrhs;
   a.out_par = out_par;
-  a.in = in;
-  a.out = out;
   a.c = 1.0;
   a.reduce = RED_NONE;
   a.pstride = (size_t)S.nblocks_max;
   for (int l = 0; l < B.nlat; ++l) {
     const lq_gauge* g = hi ? B.hi[l] : B.lo[l];
+    const size_t off = B.voff[l] * bps;
     a.lat[l].gauge = g->data;
     a.lat[l].blk_bytes = g->blk_bytes;
     a.lat[l].G = make_geom(g);
-    a.lat[l].voff = B.voff[l];
+    a.lat[l].in = (const char*)in + off;
+    a.lat[l].out = (char*)out + off;
+    a.lat[l].w1 = w1 ? (const char*)w1 + off : nullptr;
+    a.lat[l].w2 = w2 ? (const char*)w2 + off : nullptr;
   }
   return a;
 }
@@ -348,25 +354,33 @@ lq_status batch_iteration_dslash(Solver& S) {
   MultiKArgs d = multi_args(S, false, 1, S.p, S.t);
   lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
   if (st) return st;
-  MultiKArgs e = multi_args(S, false, 0, S.t, S.Ap);
-  e.w1 = S.p;
+  MultiKArgs e = multi_args(S, false, 0, S.t, S.Ap, S.p);
   for (int l = 0; l < B.nlat; ++l) e.lat[l].a1 = B.mass[l] * B.mass[l];
   e.c = -1.0;
   e.reduce = RED_DOT;
   e.red = S.reducer(FIN_ALPHA);
   e.skip_state = S.sc;
+  e.skip_mode = SKIP_INACTIVE;
   return launch_dslash_multi(S.ctx, e, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
 }
 
-lq_status batch_true_residual(Solver& S) {
+// skip_done: leave out the lattices whose systems have all met the tolerance already
+// (their residual and norm entries are then not rewritten).
+lq_status batch_true_residual(Solver& S, bool skip_done) {
   const Batch& B = *S.batch;
   const lq_gauge* g0 = B.hi[0];
   MultiKArgs d = multi_args(S, true, 1, S.x, S.thi);
+  if (skip_done) {
+    d.skip_state = S.sc;
+    d.skip_mode = SKIP_DONE;
+  }
   lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, LQ_F64, B.key_hi, S.s);
   if (st) return st;
-  MultiKArgs e = multi_args(S, true, 0, S.thi, S.rhi);
-  e.w1 = S.b;
-  e.w2 = S.x;
+  MultiKArgs e = multi_args(S, true, 0, S.thi, S.rhi, S.b, S.x);
+  if (skip_done) {
+    e.skip_state = S.sc;
+    e.skip_mode = SKIP_DONE;
+  }
   for (int l = 0; l < B.nlat; ++l) {
     e.lat[l].a1 = 1.0;
     e.lat[l].a2 = -B.mass[l] * B.mass[l];
@@ -444,8 +458,8 @@ lq_status iteration(Solver& S) {
 }
 
 // r_hi = b - M x_hi in FP64 and ||r_hi||^2 -> result (FIN_STORE).
-lq_status true_residual(Solver& S) {
-  if (S.batch) return batch_true_residual(S);
+lq_status true_residual(Solver& S, bool skip_done = false) {
+  if (S.batch) return batch_true_residual(S, skip_done);
   DslashArgs d;
   d.U = S.Uhi;
   d.in = S.x;
@@ -570,7 +584,8 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
   const int n = S.nsys;
   const double tol2 = P.tol * P.tol;
   std::vector<double> res;
-  std::vector<int> done(n, 0), updates(n, 0), frozen_iters(n, 0);
+  std::vector<int> done(n, 0), updates(n, 0);
+  std::vector<double> final_r2(n, 0.0);  // FP64 true residual^2 of each system once done
   std::vector<double> bb(n);
   lq_status st;
 
@@ -599,7 +614,7 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     c.rhi2 = bb[i];
     c.beta = 0.0;           // first xpay: p = r
     c.active = bb[i] > 0.0;
-    if (bb[i] == 0.0) done[i] = 1;  // x = 0 solves it exactly
+    if (bb[i] == 0.0) done[i] = c.done = 1;  // x = 0 solves it exactly
   }
   st = push_scalars(S);
   if (st) return st;
@@ -654,7 +669,7 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     if (!need) continue;
     st = fold_x(S);
     if (st) return st;
-    st = true_residual(S);
+    st = true_residual(S, /*skip_done=*/true);
     if (st) return st;
     std::vector<double> rhi2;
     st = read_result(S, rhi2);
@@ -673,8 +688,9 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
       if (!isfinite(rhi2[i])) return lq_fail(ctx, LQ_ERR_NUMERIC, "true residual of rhs %d is NaN/Inf", i);
       if (rhi2[i] <= tol2 * bb[i]) {
         done[i] = 1;
+        c.done = 1;
         c.active = 0;
-        frozen_iters[i] = c.iters;
+        final_r2[i] = rhi2[i];
         continue;
       }
       if (!c.active) restarted = true;
@@ -687,13 +703,20 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     st = push_scalars(S);
     if (st) return st;
   }
-  // ---- final true residuals
-  st = fold_x(S);
-  if (st) return st;
-  st = true_residual(S);
-  if (st) return st;
-  st = read_result(S, res);
-  if (st) return st;
+  // ---- final true residuals: a done system's x has not changed since its last FP64 check,
+  // so the residual of that check stands; the others are recomputed.
+  bool all_done = true;
+  for (int i = 0; i < n; ++i) all_done &= done[i] != 0;
+  if (all_done) {
+    res = final_r2;
+  } else {
+    st = fold_x(S);
+    if (st) return st;
+    st = true_residual(S);
+    if (st) return st;
+    st = read_result(S, res);
+    if (st) return st;
+  }
   int all = 1;
   for (int i = 0; i < n; ++i) {
     double rel = bb[i] > 0 ? sqrt(res[i] / bb[i]) : 0.0;

@@ -7,6 +7,12 @@
 #include "dslash_kernel.cuh"
 #include "dslash_multi.cuh"
 
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
 static const char* prec_name(lq_prec p) {
   switch (p) {
     case LQ_F64: return "f64";
@@ -119,11 +125,6 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   return LQ_OK;
 }
 
-static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
-  const char* pa = (const char*)a;
-  const char* pb = (const char*)b;
-  return pa < pb + nb && pb < pa + na;
-}
 
 extern "C" lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
                                int out_parity, int nrhs, lq_prec vec_prec, lq_stream stream) {
@@ -179,7 +180,7 @@ static std::vector<TuneEntry> multi_candidates(lq_prec gp, int nrhs) {
   c.push_back(d);
   for (int t : {1, 2, 4, 8}) {
     if (t > nrhs || (gp == LQ_F64 && t > 4)) continue;
-    for (int tps : {1, 2})
+    for (int tps : {1, 2, 4})
       for (int b : {64, 128, 256}) {
         if (!dslash_multi_shape_ok(t, tps) || (b == 128 && t == first_tile && tps == 1)) continue;
         TuneEntry e;
@@ -197,20 +198,26 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
   MultiLaunchFn fn = dslash_multi_fn(gp, recon);
   if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
   MultiKArgs plain = a;
-  plain.w1 = plain.w2 = nullptr;
+  for (int l = 0; l < a.nlat; ++l) plain.lat[l].w1 = plain.lat[l].w2 = nullptr;
   plain.c = 1.0;
   plain.reduce = RED_NONE;
   plain.skip_state = nullptr;
   TuneEntry pick;
-  lq_status st = tune_pick(
-      ctx, key, multi_candidates(gp, a.nrhs), s,
-      [&](const TuneEntry& c) -> lq_status {
-        cudaError_t e = fn(plain, vp, c.block, c.rhs_tile, c.tps, ctx->num_sms, s);
-        if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi (tuning)");
-        return LQ_OK;
-      },
-      &pick);
-  if (st) return st;
+  const TuneEntry& f = ctx->forced;
+  if (f.block && dslash_multi_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
+      !(gp == LQ_F64 && f.rhs_tile > 4)) {
+    pick = f;
+  } else {
+    lq_status st = tune_pick(
+        ctx, key, multi_candidates(gp, a.nrhs), s,
+        [&](const TuneEntry& c) -> lq_status {
+          cudaError_t e = fn(plain, vp, c.block, c.rhs_tile, c.tps, ctx->num_sms, s);
+          if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi (tuning)");
+          return LQ_OK;
+        },
+        &pick);
+    if (st) return st;
+  }
   if (a.reduce != RED_NONE) {
     MultiKArgs chk = a;
     multi_tiles(chk, pick.block, pick.rhs_tile, pick.tps);
@@ -221,4 +228,50 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
   cudaError_t e = fn(a, vp, pick.block, pick.rhs_tile, pick.tps, ctx->num_sms, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi");
   return LQ_OK;
+}
+
+extern "C" lq_status dslash_eo_multi(lq_context* ctx, int nlat, const lq_gauge* const* U, const void* const* in,
+                                     void* const* out, int out_parity, int nrhs, lq_prec vec_prec,
+                                     lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (nlat < 1 || nlat > kMaxLat) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nlat must be in [1, %d]", kMaxLat);
+  if (!U || !in || !out) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL array argument");
+  if (out_parity != 0 && out_parity != 1) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "out_parity must be 0 or 1");
+  if (nrhs < 1 || nrhs > 16) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "nrhs must be in [1, 16]");
+  for (int l = 0; l < nlat; ++l) {
+    if (!U[l]) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U[%d] is NULL", l);
+    if (U[l]->prec != U[0]->prec || U[l]->recon != U[0]->recon)
+      return lq_fail(ctx, LQ_ERR_INVALID_ARG, "all gauges must share precision and recon");
+    if (!in[l] || !out[l] || !lq_aligned16(in[l]) || !lq_aligned16(out[l]))
+      return lq_fail(ctx, LQ_ERR_INVALID_ARG, "in[%d]/out[%d] must be non-NULL 16-byte aligned", l, l);
+    const size_t vb = (size_t)nrhs * U[l]->Vh * 6 * lq_prec_bytes(vec_prec);
+    if (overlap(in[l], vb, out[l], vb)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "in[%d] and out[%d] overlap", l, l);
+  }
+  const lq_prec gp = U[0]->prec;
+  if ((gp == LQ_F64 && vec_prec != LQ_F64) || (gp != LQ_F64 && vec_prec != LQ_F32))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "dslash_eo_multi pairs LQ_F64 links with LQ_F64 vectors and "
+                                            "reduced-precision links with LQ_F32 vectors");
+  DeviceGuard dg(ctx->device);
+  MultiKArgs a;
+  memset(&a, 0, sizeof a);
+  a.nlat = nlat;
+  a.nrhs = nrhs;
+  a.out_par = out_parity;
+  a.c = 1.0;
+  a.reduce = RED_NONE;
+  std::string lats;
+  for (int l = 0; l < nlat; ++l) {
+    a.lat[l].gauge = U[l]->data;
+    a.lat[l].blk_bytes = U[l]->blk_bytes;
+    a.lat[l].G = make_geom(U[l]);
+    a.lat[l].in = in[l];
+    a.lat[l].out = out[l];
+    char d[64];
+    snprintf(d, sizeof d, "%s%dx%dx%dx%d", l ? "," : "", U[l]->dims[0], U[l]->dims[1], U[l]->dims[2], U[l]->dims[3]);
+    lats += d;
+  }
+  char key[512];
+  snprintf(key, sizeof key, "dslash_multi g=%s/%d v=%s lats=%s nrhs=%d", prec_name(gp), (int)U[0]->recon,
+           prec_name(vec_prec), lats.c_str(), nrhs);
+  return launch_dslash_multi(ctx, a, gp, U[0]->recon, vec_prec, key, (cudaStream_t)stream);
 }

@@ -29,15 +29,20 @@ struct DslashKArgs {
 };
 
 // One thread per (output site, direction group), TPS threads per site, NR right-hand sides
-// per thread (grid.y runs over rhs tiles).
+// per thread.  The rhs tiles of one block of sites are consecutive blocks of the grid
+// (block b: rhs tile b % ntiles_y, site block b / ntiles_y), so they are dispatched
+// together and read the same links while those are still in L2.
 template <lq_prec GP, int R, lq_prec VP, int NR, int TPS>
 __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   using T = typename LinkT<GP, R>::real;
   static_assert(TPS == 1 || TPS == 2 || TPS == 4, "TPS must be 1, 2 or 4");
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nty = (a.nrhs + NR - 1) / NR;
+  const int ty = blockIdx.x % nty;
+  const int bx = blockIdx.x / nty;
+  const int gtid = bx * blockDim.x + threadIdx.x;
   const int cb = gtid / TPS;
   const int sub = gtid % TPS;
-  const int rhs0 = blockIdx.y * NR;
+  const int rhs0 = ty * NR;
   const bool live = cb < a.G.Vh;
   double part[NR];
   T acc[NR][6];
@@ -54,7 +59,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   if (live)
     dslash_epilogue<VP, NR, TPS>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, a.reduce, a.rhs_stride, a.nrhs,
                                  rhs0, cb, sub, part);
-  if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs);
+  if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 
 // Host side: launch one instance.  Supported (rhs tile, threads per site) pairs:
@@ -67,7 +72,8 @@ inline bool dslash_shape_ok(int tile, int tps) {
 
 template <lq_prec GP, int R, lq_prec VP, int NR, int TPS>
 static cudaError_t launch_dslash_inst(const DslashKArgs& k, int block, cudaStream_t s) {
-  dim3 grid((unsigned)(((long long)k.G.Vh * TPS + block - 1) / block), (k.nrhs + NR - 1) / NR);
+  const long long nbx = ((long long)k.G.Vh * TPS + block - 1) / block;
+  dim3 grid((unsigned)(nbx * ((k.nrhs + NR - 1) / NR)));
   k_dslash<GP, R, VP, NR, TPS><<<grid, block, 0, s>>>(k);
   return cudaGetLastError();
 }

@@ -1,7 +1,7 @@
 // Multi-lattice half Dslash: one persistent launch applies the half Dslash to up to
-// kMaxLat lattices of different sizes, each with nrhs right-hand sides, whose vectors sit
-// back to back in one "concatenated" array (lattice l starts at site offset voff_l and
-// holds [nrhs][Vh_l][3]).  The work is cut into tiles (lattice, rhs tile, block of sites);
+// kMaxLat lattices of different sizes, each with nrhs right-hand sides ([nrhs][Vh_l][3]
+// vectors per lattice).  The work is cut into tiles (lattice, block of sites, rhs tile --
+// the rhs tiles of a site block adjacent, so they share its links in L2);
 // a grid of about one wave of resident blocks walks the tiles in a fixed order (no queue,
 // no waiting), so small lattices and the tail of large ones share the GPU.
 #pragma once
@@ -10,12 +10,16 @@
 #include "tune.cuh"
 
 constexpr int kMaxLat = 16;
+enum { SKIP_INACTIVE = 1, SKIP_DONE = 2 };
 
 struct MLat {
   const char* gauge;  // packed links of this lattice
   size_t blk_bytes;
   Geom G;
-  size_t voff;        // first site of this lattice in the concatenated vectors
+  const void* in;     // this lattice's vectors
+  void* out;
+  const void* w1;     // optional epilogue vectors
+  const void* w2;
   double a1, a2;      // epilogue coefficients of this lattice
   int tile0;          // first tile of this lattice
   int tiles_x;        // site blocks per rhs tile
@@ -23,14 +27,11 @@ struct MLat {
 
 struct MultiKArgs {
   int nlat, ntiles, nrhs, out_par;
-  const void* in;     // concatenated vectors
-  void* out;
-  const void* w1;
-  const void* w2;
   double c;
   int reduce;
   size_t pstride;     // partials row stride (columns per (lattice, rhs) row)
-  const CGScalars* skip_state;  // optional: tiles whose rhs are all inactive are skipped
+  const CGScalars* skip_state;  // optional per-system state: tiles whose systems are all
+  int skip_mode;                // inactive (SKIP_INACTIVE) or all done (SKIP_DONE) are skipped
   Reducer red;        // rows q = l * nrhs + rhs
   MLat lat[kMaxLat];
 };
@@ -44,12 +45,16 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
     while (l + 1 < a.nlat && tile >= a.lat[l + 1].tile0) ++l;
     const MLat& L = a.lat[l];
     const int tl = tile - L.tile0;
-    const int ty = tl / L.tiles_x, tx = tl % L.tiles_x;
+    const int nty = (a.nrhs + NR - 1) / NR;   // rhs tiles of one site block are adjacent
+    const int ty = tl % nty, tx = tl / nty;
     const int rhs0 = ty * NR;
     bool skip = false;
     if (a.skip_state) {
       skip = true;
-      for (int r = 0; r < NR && rhs0 + r < a.nrhs; ++r) skip &= !a.skip_state[l * a.nrhs + rhs0 + r].active;
+      for (int r = 0; r < NR && rhs0 + r < a.nrhs; ++r) {
+        const CGScalars& c = a.skip_state[l * a.nrhs + rhs0 + r];
+        skip &= (a.skip_mode == SKIP_DONE) ? (c.done != 0) : (c.active == 0);
+      }
     }
     double part[NR];
 #pragma unroll
@@ -59,20 +64,18 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
       const int cb = gtid / TPS;
       const int sub = gtid % TPS;
       const bool live = cb < L.G.Vh;
-      const size_t vb = VT::bytes_per_site * L.voff;
       T acc[NR][6];
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc[r][k] = T(0);
       if (live)
-        dslash_hops<GP, R, VP, NR, TPS>(L.gauge, L.blk_bytes, L.G, a.out_par, (const char*)a.in + vb, L.G.Vh,
-                                        a.nrhs, rhs0, cb, sub, acc);
+        dslash_hops<GP, R, VP, NR, TPS>(L.gauge, L.blk_bytes, L.G, a.out_par, L.in, L.G.Vh, a.nrhs, rhs0, cb,
+                                        sub, acc);
       dslash_combine<NR, TPS>(acc);
       if (live)
-        dslash_epilogue<VP, NR, TPS>(acc, (char*)a.out + vb, a.w1 ? (const char*)a.w1 + vb : nullptr, L.a1,
-                                     a.w2 ? (const char*)a.w2 + vb : nullptr, L.a2, a.c, a.reduce, L.G.Vh,
-                                     a.nrhs, rhs0, cb, sub, part);
+        dslash_epilogue<VP, NR, TPS>(acc, L.out, L.w1, L.a1, L.w2, L.a2, a.c, a.reduce, L.G.Vh, a.nrhs, rhs0, cb,
+                                     sub, part);
     }
     if (a.reduce != RED_NONE) {
       const int nvalid = a.nrhs - rhs0 < NR ? a.nrhs - rhs0 : NR;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
 
 // Launch-shape helpers -----------------------------------------------------------------
 inline bool dslash_multi_shape_ok(int tile, int tps) {
-  return (tile == 1 || tile == 2 || tile == 4 || tile == 8) && (tps == 1 || tps == 2) && !(tile == 8 && tps == 2);
+  return (tile == 1 || tile == 2 || tile == 4 || tile == 8) && (tps == 1 || tps == 2 || tps == 4);
 }
 
 // Fills the tile bookkeeping of `a` for a launch shape; returns the number of tiles.
@@ -120,11 +123,16 @@ static cudaError_t launch_multi_shape(const MultiKArgs& a, int block, int tile, 
   switch (tile * 8 + tps) {
     case 1 * 8 + 1: return launch_multi_inst<GP, R, VP, 1, 1>(a, block, num_sms, s);
     case 1 * 8 + 2: return launch_multi_inst<GP, R, VP, 1, 2>(a, block, num_sms, s);
+    case 1 * 8 + 4: return launch_multi_inst<GP, R, VP, 1, 4>(a, block, num_sms, s);
     case 2 * 8 + 1: return launch_multi_inst<GP, R, VP, 2, 1>(a, block, num_sms, s);
     case 2 * 8 + 2: return launch_multi_inst<GP, R, VP, 2, 2>(a, block, num_sms, s);
+    case 2 * 8 + 4: return launch_multi_inst<GP, R, VP, 2, 4>(a, block, num_sms, s);
     case 4 * 8 + 1: return launch_multi_inst<GP, R, VP, 4, 1>(a, block, num_sms, s);
     case 4 * 8 + 2: return launch_multi_inst<GP, R, VP, 4, 2>(a, block, num_sms, s);
+    case 4 * 8 + 4: return launch_multi_inst<GP, R, VP, 4, 4>(a, block, num_sms, s);
     case 8 * 8 + 1: return launch_multi_inst<GP, R, VP, 8, 1>(a, block, num_sms, s);
+    case 8 * 8 + 2: return launch_multi_inst<GP, R, VP, 8, 2>(a, block, num_sms, s);
+    case 8 * 8 + 4: return launch_multi_inst<GP, R, VP, 8, 4>(a, block, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -57,24 +57,26 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
     // forward hop: U_mu(x) in(x+mu); U_mu(x) lives in block (mu, out_par) at cb
     L::load(gauge + (size_t)(2 * mu + out_par) * blk_bytes, G.S, cb, u);
     if (R == 12) reconstruct_row2(u);
+    {
+      T v[NR][6];  // all loads of the hop issued before any arithmetic
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (rhs0 + r < nrhs) {
-        T v[6];
-        VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbf, v);
-        mat_vec_acc(u, v, acc[r], eta);
-      }
+      for (int r = 0; r < NR; ++r)
+        if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbf, v[r]);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (rhs0 + r < nrhs) mat_vec_acc(u, v[r], acc[r], eta);
     }
     // backward hop: U_mu(x-mu)^dag in(x-mu); that link lives in block (mu, 1-out_par)
     L::load(gauge + (size_t)(2 * mu + opar) * blk_bytes, G.S, cbb, u);
     if (R == 12) reconstruct_row2(u);
+    {
+      T v[NR][6];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (rhs0 + r < nrhs) {
-        T v[6];
-        VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbb, v);
-        adj_mat_vec_acc(u, v, acc[r], -eta);
-      }
+      for (int r = 0; r < NR; ++r)
+        if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbb, v[r]);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (rhs0 + r < nrhs) adj_mat_vec_acc(u, v[r], acc[r], -eta);
     }
   }
 }

@@ -95,7 +95,8 @@ struct CGScalars {
   double rhi2;    // ||r||^2 of the last FP64 residual replacement
   int active;     // 1 while iterating
   int iters;      // iterations done while active
-  int pad[2];
+  int done;       // set by the host once the FP64 true residual met the tolerance
+  int pad;
 };
 
 enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
@@ -129,11 +130,12 @@ __device__ __forceinline__ double warp_sum(double x) {
 }
 
 // Every thread of the block calls this with its NR per-rhs contributions (rhs0 + r).
-// Partials go to red.partials[rhs][blockIdx.x]; the last block to arrive sums them in
-// block order (deterministic for a given launch shape) and runs the finisher.  No thread
-// ever waits on another block.
+// Partials go to red.partials[rhs][bx] (bx < nbx: the block's column); the last block of
+// the grid to arrive sums them in column order (deterministic for a given launch shape)
+// and runs the finisher.  No thread ever waits on another block.
 template <int NR>
-__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs) {
+__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs,
+                                             int bx, int nbx) {
   __shared__ double sm[NR][32];
   __shared__ int am_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -143,13 +145,12 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
     if (lane == 0) sm[r][warp] = x;
   }
   __syncthreads();
-  const int nbx = gridDim.x;
   if (warp == 0) {
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       double x = lane < nw ? sm[r][lane] : 0.0;
       x = warp_sum(x);
-      if (lane == 0 && rhs0 + r < nrhs) red.partials[(size_t)(rhs0 + r) * nbx + blockIdx.x] = x;
+      if (lane == 0 && rhs0 + r < nrhs) red.partials[(size_t)(rhs0 + r) * nbx + bx] = x;
     }
   }
   __threadfence();
@@ -169,6 +170,12 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
     if (lane == 0) finish_one(red, rhs, x);
   }
   if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// The one-dimensional form: column = blockIdx.x of a (nbx, rhs tiles) grid.
+template <int NR>
+__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs) {
+  block_reduce<NR>(v, red, rhs0, nrhs, blockIdx.x, gridDim.x);
 }
 
 // Block-wide sums of v[r] (every thread calls); thread 0 stores sum r at dst[r * stride]

@@ -101,3 +101,25 @@ def test_invalid_arguments(lq, ctx):
         lq.dslash_eo(ctx, g, a, a, 0, 1)           # in and out overlap
     with pytest.raises(lq.LQError, match="INVALID_ARG"):
         lq.dslash_eo(ctx, g, a, empty_vec((1, 128, 3), "f64"), 0, 1, vec_prec=lq.LQ_F64)
+
+
+@pytest.mark.parametrize("gp,recon,vp", [("f64", 18, "f64"), ("f32", 12, "f32"), ("bf16", 18, "f32"),
+                                         ("f16", 12, "f32")])
+@pytest.mark.parametrize("nrhs", [1, 5, 8])
+def test_dslash_multi_matches_single(lq, ctx, gp, recon, vp, nrhs):
+    import torch
+    dims_list = [(4, 4, 4, 4), (6, 4, 2, 10), (8, 8, 8, 8), (2, 2, 2, 2)]
+    Us, ins, outs, refs = [], [], [], []
+    for i, dims in enumerate(dims_list):
+        U = synth.gauge_field(dims, "haar", seed=140 + i)
+        chi = synth.fermion_field(dims, nrhs, seed=150 + i)
+        g = lq.lq_gauge_pack(ctx, dims, torch.from_numpy(U).cuda(), gp, recon)
+        cd = to_device_vec(chi, vp)
+        Us.append(g)
+        ins.append(cd)
+        outs.append(empty_vec(chi.shape, vp))
+        refs.append(odslash.dslash_eo_multi(quantize_links(U, gp, recon), from_device_vec(cd), dims, 1))
+    lq.dslash_eo_multi(ctx, Us, ins, outs, 1, nrhs)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert rel_l2(from_device_vec(o), r) < store_tolerance(vp)
