@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cg-maxiter", type=int, default=20000,
+                   help="iteration cap of the CG comparison (small values: short runs for profiling)")
+    p.add_argument("--no-batched-force", action="store_true")
     return p.parse_args()
 
 
@@ -310,8 +313,37 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
                                        "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
         del gauges, ins, ts, outs
         torch.cuda.empty_cache()
-    # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
+    # multi-RHS Dslash (links loaded once per site for all right-hand sides)
     import synth
+    for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
+        sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
+        K = ring_size(Vh * sb, l2, nstreams)
+        gauges = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
+        chi = torch.from_numpy(synth.fermion_field(DIMS, nrhs, seed=12)).to(torch.complex64)
+        ins = [chi.cuda() for _ in range(K)]
+        ts = [torch.empty_like(ins[0]) for _ in range(K)]
+        outs = [torch.empty_like(ins[0]) for _ in range(K)]
+
+        def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs):
+            h = 0
+            for a in range(10):
+                s_ = ss[a % len(ss)]
+                c, c2 = h % K, (h + 1) % K
+                lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
+                lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
+                h += 2
+            return 20
+        g = GraphStep(torch, mstep, nstreams)
+        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+        del g
+        us = ms * 1000.0 / launches
+        gbs = Vh * sb / us / 1e3
+        out[f"multi_rhs/{prec}/{recon}/nrhs{nrhs}"] = {
+            "gflops": round(Vh * nrhs * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+            "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+        del gauges, ins, ts, outs
+        torch.cuda.empty_cache()
+    # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
     n = 4 * 2 * Vh
     A = torch.from_numpy(synth.haar_su3(synth.rng(9), n))
     b = torch.from_numpy(synth.complex_gaussian(synth.rng(10), (n, 3)))
@@ -334,10 +366,37 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
             out[f"su3_matvec/{prec}/adj{adj}"] = {"gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1),
                                                   "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
         del As, bs, cs
+    # mult_su3_nn / an / na over the 4V links (pairs of Haar matrices)
+    B2 = torch.from_numpy(synth.haar_su3(synth.rng(11), n))
+    for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
+        per = n * 54 * BYTES[prec]
+        K = ring_size(per, l2)
+        As = [A.to(dt).cuda() for _ in range(K)]
+        Bs = [B2.to(dt).cuda() for _ in range(K)]
+        Cs = [torch.empty_like(As[0]) for _ in range(K)]
+        for adjA, adjB in ((0, 0), (1, 0), (0, 1)):
+            def step(ss):
+                for i in range(20):
+                    lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[0])
+                return 20
+            g = GraphStep(torch, step, 1)
+            ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = per / us / 1e3
+            out[f"su3_mul/{prec}/adj{adjA}{adjB}"] = {"gflops": round(n * 198 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                     "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
+        del As, Bs, Cs
+    # the 1024-pair FP64 product of the 4^4 configuration: latency of one call
+    Ad, Bd = A[:1024].cuda(), B2[:1024].cuda()
+    Cd = torch.empty_like(Ad)
+    g = GraphStep(torch, lambda ss: [lq.su3_mul_batch(ctx, Ad, Bd, Cd, 1024, 0, 0, None, ss[0]) for _ in range(20)] and 20, 1)
+    ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+    out["su3_mul/f64/1024_pairs_us"] = round(ms * 1000.0 / launches, 2)
     return out
 
 
-def run_cg(lq, ctx, torch):
+def run_cg(lq, ctx, torch, maxiter=20000):
     """32^4, Haar links, m = 0.01, Gaussian source: FP64 CG against mixed precision."""
     import synth
     dims, mass = (32, 32, 32, 32), 0.01
@@ -356,7 +415,7 @@ def run_cg(lq, ctx, torch):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         try:
-            st = lq.cg_solve(ctx, hi, lo, mass, b, x, 1, tol=1e-10, maxiter=20000)[0]
+            st = lq.cg_solve(ctx, hi, lo, mass, b, x, 1, tol=1e-10, maxiter=maxiter)[0]
             ok = True
         except lq.LQError as e:
             st, ok = e.stats[0], False
@@ -456,6 +515,7 @@ def run_ours(args):
     device = torch.device("cuda", local)
     lq.load()  # raises if the library has not been built (__graft_entry__.build())
     ctx = lq.Context(local)
+    ctx.set_tuning(2)  # launch shapes for several applications in flight (--streams)
     stream = torch.cuda.current_stream()
     prec, recon = args.prec, args.recon
     vec = args.vec or ("f64" if prec == "f64" else "f32")
@@ -503,12 +563,14 @@ def run_ours(args):
     vbytes = ins[0].numel() * ins[0].element_size()
 
     extra = {}
-    if rank == 0 and not args.no_variants:
+    if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
         extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream, args.streams)
     if rank == 0 and not args.no_cg:
-        extra["cg"] = run_cg(lq, ctx, torch)
-        extra["batched"] = run_batched(lq, ctx, torch)
-        extra["force"] = run_force(lq, ctx, torch)
+        ctx.set_tuning(1)  # the solvers issue one launch at a time
+        extra["cg"] = run_cg(lq, ctx, torch, args.cg_maxiter)
+        if not args.no_batched_force:
+            extra["batched"] = run_batched(lq, ctx, torch)
+            extra["force"] = run_force(lq, ctx, torch)
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -539,6 +601,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     line["config"]["streams"] = args.streams
+    line["config"]["tuning"] = "autotuned, throughput mode (lq_set_tuning 2)"
     line["config"]["launch_shape"] = [l for l in ctx.tune_report().splitlines()
                                       if f"g={prec}/{recon} v={vec} dims=16x16x16x32 nrhs=1" in l]
     line.update(extra)

@@ -75,13 +75,17 @@ lq_status lq_destroy(lq_context* ctx);
 const char* lq_last_error(const lq_context* ctx);
 /* Name of a status code. */
 const char* lq_status_string(lq_status s);
-/* Autotuning of launch shapes (block size, right-hand sides per thread): 1 = on (the
- * default, unless the environment sets LQCD_TUNE=0), 0 = fixed defaults.  Tuning times
- * candidate launches on the first call with a new shape key and must not happen during
- * stream capture: make one uncaptured call with the same shapes first.  The environment
- * variable LQCD_DSLASH_SHAPE="block,rhs_tile,threads_per_site" forces one shape for every
- * single-lattice Dslash launch it fits (block 64..256, a multiple of 32). */
-lq_status lq_set_tuning(lq_context* ctx, int enable);
+/* Autotuning of launch shapes (threads per block, right-hand sides per thread, threads per
+ * site).  mode 0: off, fixed defaults.  mode 1 (the default, unless the environment sets
+ * LQCD_TUNE=0): each new shape key is tuned on its first call by timing every candidate
+ * as a lone launch after an L2 flush; among the candidates within 3% of the fastest the
+ * one with the least redundant work wins.  mode 2: the same, with a 15% margin -- for
+ * callers that keep several independent launches in flight (streams, graphs), where a
+ * launch's own parallelism matters less than its instruction count.  Tuning must not
+ * happen during stream capture: make one uncaptured call with the same shapes first.  The
+ * environment variable LQCD_DSLASH_SHAPE="block,rhs_tile,threads_per_site" forces one
+ * shape for every Dslash launch it fits (block 64..256, a multiple of 32). */
+lq_status lq_set_tuning(lq_context* ctx, int mode);
 /* Write the tuning table (one line per key: key, chosen block, rhs tile, microseconds)
  * into buf (NUL-terminated, truncated to len).  *needed receives the full length + 1. */
 lq_status lq_tune_report(const lq_context* ctx, char* buf, size_t len, size_t* needed);

@@ -129,8 +129,9 @@ class Context:
         except Exception:
             pass
 
-    def set_tuning(self, enable: bool):
-        self.check(self.lib.lq_set_tuning(self.handle, int(bool(enable))))
+    def set_tuning(self, mode):
+        """0/False: off; 1/True: shapes for lone launches; 2: for concurrent launches."""
+        self.check(self.lib.lq_set_tuning(self.handle, int(mode)))
 
     def tune_report(self) -> str:
         need = ctypes.c_size_t()

@@ -91,9 +91,11 @@ extern "C" lq_status lq_destroy(lq_context* ctx) {
   return LQ_OK;
 }
 
-extern "C" lq_status lq_set_tuning(lq_context* ctx, int enable) {
+extern "C" lq_status lq_set_tuning(lq_context* ctx, int mode) {
   if (!ctx) return LQ_ERR_INVALID_ARG;
-  ctx->tuning = enable != 0;
+  if (mode < 0 || mode > 2) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "tuning mode must be 0, 1 or 2");
+  ctx->tuning = mode != 0;
+  if (mode) ctx->tune_mode = mode;
   return LQ_OK;
 }
 

@@ -17,7 +17,10 @@
 
 #include "lqcd_internal.cuh"
 
-// Accumulates the hops of this thread's directions into acc (zeroed by the caller).
+// Accumulates the hops of this thread's directions into acc (zeroed by the caller).  Per
+// hop: the link, then the neighbour vectors of every right-hand side, then the arithmetic.
+// (Issuing both hops' loads first, or the next direction's loads before this direction's
+// arithmetic, was measured: the extra registers cost more occupancy than they gained.)
 template <lq_prec GP, int R, lq_prec VP, int NR, int TPS, class T>
 __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size_t blk_bytes, const Geom& G,
                                             int out_par, const void* __restrict__ in, size_t rhs_stride,
@@ -58,7 +61,7 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
     L::load(gauge + (size_t)(2 * mu + out_par) * blk_bytes, G.S, cb, u);
     if (R == 12) reconstruct_row2(u);
     {
-      T v[NR][6];  // all loads of the hop issued before any arithmetic
+      T v[NR][6];
 #pragma unroll
       for (int r = 0; r < NR; ++r)
         if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbf, v[r]);

@@ -26,6 +26,19 @@ template <class T> __device__ __forceinline__ C2<T> cmul_conj(C2<T> a, C2<T> b) 
   return {a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i};
 }
 
+// Copies `nreal` reals from shared to global memory with 16-byte stores (both 16-byte
+// aligned; the block's slice starts at a multiple of kForceThreads links).
+template <class T>
+__device__ __forceinline__ void store_slice(T* __restrict__ dst, const T* __restrict__ src, int nreal) {
+  constexpr int W = 16 / sizeof(T);
+  const int nvec = nreal / W;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+  for (int i = nvec * W + threadIdx.x; i < nreal; i += blockDim.x) dst[i] = src[i];
+}
+
+// One thread per link (mu = blockIdx.y, lex); G and F leave through shared memory so that
+// each block writes its contiguous slice of the [4][V][3][3] outputs with coalesced stores.
 template <lq_prec P>
 __global__ void __launch_bounds__(kForceThreads) k_force(const char* __restrict__ gauge, size_t blk_bytes, Geom G,
                                                          const void* __restrict__ chi, const void* __restrict__ psi,
@@ -33,53 +46,56 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const char* __restrict_
   using L = LinkT<P, 18>;
   using VT = VecT<P>;
   using T = typename L::real;
+  __shared__ __align__(16) T stage[kForceThreads * 18];
   const int V = 2 * G.Vh;
-  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lex0 = blockIdx.x * blockDim.x;
+  const int lex = lex0 + threadIdx.x;
   const int mu = blockIdx.y;
-  if (lex >= V) return;
-  const int x = lex % G.Lx;
-  int rest = lex / G.Lx;
-  const int y = rest % G.Ly;
-  rest /= G.Ly;
-  const int z = rest % G.Lz;
-  const int t = rest / G.Lz;
-  const int par = (x + y + z + t) & 1;
-  const int cb = lex >> 1;
-  // neighbour y + mu
-  int c[4] = {x, y, z, t};
-  const int Ls[4] = {G.Lx, G.Ly, G.Lz, G.Lt};
-  c[mu] = (c[mu] + 1 == Ls[mu]) ? 0 : c[mu] + 1;
-  const int lexf = c[0] + G.Lx * (c[1] + G.Ly * (c[2] + G.Lz * c[3]));
-  const int cbf = lexf >> 1;
-  const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
-  const T eta = (ephase & 1) ? T(-1) : T(1);
-  // a = left vector, b = right vector of the outer product Z = s * a b^dag
-  T a[6], b[6];
-  T s;
-  if (par) {  // y odd: chi(y+mu) psi(y)^dag
-    VT::load(chi, cbf, a);
-    VT::load(psi, cb, b);
-    s = eta;
-  } else {    // y even: -psi(y+mu) chi(y)^dag
-    VT::load(psi, cbf, a);
-    VT::load(chi, cb, b);
-    s = -eta;
-  }
-  T u[18];
-  L::load(gauge + (size_t)(2 * mu + par) * blk_bytes, G.S, cb, u);
-  // Z_ij = s a_i conj(b_j)
-  C2<T> Z[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      C2<T> p = cmul_conj(C2<T>{a[2 * i], a[2 * i + 1]}, C2<T>{b[2 * j], b[2 * j + 1]});
-      Z[i][j] = {s * p.r, s * p.i};
+  const int nlinks = min((int)blockDim.x, V - lex0);
+  const bool live = lex < V;
+  T g[18], f[18];
+  if (live) {
+    const int x = lex % G.Lx;
+    int rest = lex / G.Lx;
+    const int y = rest % G.Ly;
+    rest /= G.Ly;
+    const int z = rest % G.Lz;
+    const int t = rest / G.Lz;
+    const int par = (x + y + z + t) & 1;
+    const int cb = lex >> 1;
+    // neighbour y + mu (periodic)
+    const int xf = (mu == 0) ? (x + 1 == G.Lx ? 0 : x + 1) : x;
+    const int yf = (mu == 1) ? (y + 1 == G.Ly ? 0 : y + 1) : y;
+    const int zf = (mu == 2) ? (z + 1 == G.Lz ? 0 : z + 1) : z;
+    const int tf = (mu == 3) ? (t + 1 == G.Lt ? 0 : t + 1) : t;
+    const int lexf = xf + G.Lx * (yf + G.Ly * (zf + G.Lz * tf));
+    const int cbf = lexf >> 1;
+    const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+    const T eta = (ephase & 1) ? T(-1) : T(1);
+    // a = left vector, b = right vector of the outer product Z = s * a b^dag
+    T a[6], b[6];
+    T s;
+    if (par) {  // y odd: chi(y+mu) psi(y)^dag
+      VT::load(chi, cbf, a);
+      VT::load(psi, cb, b);
+      s = eta;
+    } else {    // y even: -psi(y+mu) chi(y)^dag
+      VT::load(psi, cbf, a);
+      VT::load(chi, cb, b);
+      s = -eta;
     }
-  const size_t link = (size_t)mu * V + lex;
-  if (dSdU) {
+    T u[18];
+    L::load(gauge + (size_t)(2 * mu + par) * blk_bytes, G.S, cb, u);
+    // Z_ij = s a_i conj(b_j)
+    C2<T> Z[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C2<T> p = cmul_conj(C2<T>{a[2 * i], a[2 * i + 1]}, C2<T>{b[2 * j], b[2 * j + 1]});
+        Z[i][j] = {s * p.r, s * p.i};
+      }
     // G = 2 Z^dag: G_ij = 2 conj(Z_ji)
-    T g[18];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -87,47 +103,50 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const char* __restrict_
         g[2 * (3 * i + j)] = T(2) * Z[j][i].r;
         g[2 * (3 * i + j) + 1] = -T(2) * Z[j][i].i;
       }
-    T* out = reinterpret_cast<T*>(dSdU) + link * 18;
+    {
+      // A = U G^dag = 2 U Z
+      C2<T> A[3][3];
 #pragma unroll
-    for (int k = 0; k < 18; k += 2) {
-      if constexpr (sizeof(T) == 8) reinterpret_cast<double2*>(out)[k / 2] = make_double2(g[k], g[k + 1]);
-      else reinterpret_cast<float2*>(out)[k / 2] = make_float2(g[k], g[k + 1]);
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T re = 0, im = 0;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const T ur = u[2 * (3 * i + k)], ui = u[2 * (3 * i + k) + 1];
+            re = fma(ur, Z[k][j].r, re);
+            re = fma(-ui, Z[k][j].i, re);
+            im = fma(ur, Z[k][j].i, im);
+            im = fma(ui, Z[k][j].r, im);
+          }
+          A[i][j] = {T(2) * re, T(2) * im};
+        }
+      // TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6 * 1; Tr(A - A^dag) = 2i Im Tr A
+      const T trim = (A[0][0].i + A[1][1].i + A[2][2].i) / T(3);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          f[2 * (3 * i + j)] = T(0.5) * (A[i][j].r - A[j][i].r);
+          f[2 * (3 * i + j) + 1] = T(0.5) * (A[i][j].i + A[j][i].i) - (i == j ? trim : T(0));
+        }
     }
+  }  // live
+  const size_t slice = ((size_t)mu * V + lex0) * 18;  // first real of this block's links
+  if (dSdU) {
+    if (live)
+#pragma unroll
+      for (int k = 0; k < 18; ++k) stage[threadIdx.x * 18 + k] = g[k];
+    __syncthreads();
+    store_slice(reinterpret_cast<T*>(dSdU) + slice, stage, nlinks * 18);
+    __syncthreads();
   }
   if (fta) {
-    // A = U G^dag = 2 U Z
-    C2<T> A[3][3];
+    if (live)
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        T re = 0, im = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const T ur = u[2 * (3 * i + k)], ui = u[2 * (3 * i + k) + 1];
-          re = fma(ur, Z[k][j].r, re);
-          re = fma(-ui, Z[k][j].i, re);
-          im = fma(ur, Z[k][j].i, im);
-          im = fma(ui, Z[k][j].r, im);
-        }
-        A[i][j] = {T(2) * re, T(2) * im};
-      }
-    // TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6 * 1; Tr(A - A^dag) = 2i Im Tr A
-    const T trim = (A[0][0].i + A[1][1].i + A[2][2].i) / T(3);
-    T f[18];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        f[2 * (3 * i + j)] = T(0.5) * (A[i][j].r - A[j][i].r);
-        f[2 * (3 * i + j) + 1] = T(0.5) * (A[i][j].i + A[j][i].i) - (i == j ? trim : T(0));
-      }
-    T* out = reinterpret_cast<T*>(fta) + link * 18;
-#pragma unroll
-    for (int k = 0; k < 18; k += 2) {
-      if constexpr (sizeof(T) == 8) reinterpret_cast<double2*>(out)[k / 2] = make_double2(f[k], f[k + 1]);
-      else reinterpret_cast<float2*>(out)[k / 2] = make_float2(f[k], f[k + 1]);
-    }
+      for (int k = 0; k < 18; ++k) stage[threadIdx.x * 18 + k] = f[k];
+    __syncthreads();
+    store_slice(reinterpret_cast<T*>(fta) + slice, stage, nlinks * 18);
   }
 }
 

@@ -28,6 +28,7 @@ struct lq_context {
   size_t l2_bytes = 0;
   std::string last_error;
   bool tuning = true;
+  int tune_mode = 1;            // 1: shapes for lone launches, 2: for concurrent launches
   std::map<std::string, TuneEntry> tune;
   // scratch: reductions (per-block partials, counters), CG scalars, vectors
   void* scratch = nullptr;
@@ -84,18 +85,26 @@ template <class T> struct Cplx { T re, im; };
 // 4 bytes) so a warp reads 32 consecutive chunks: fully coalesced vector loads.
 template <lq_prec P, int R> struct LinkT;
 
+// Each format offers load_raw() (the stored chunks, undecoded: issued early, cheap to
+// hold), decode() (to reals) and load() = decode(load_raw()).
 template <int R> struct LinkT<LQ_F64, R> {
   using real = double;
   static constexpr int NREAL = R;
   static constexpr size_t bytes_per_site = R * 8;
-  __device__ __forceinline__ static void load(const char* blk, int S, int cb, double* u) {
+  struct Raw { double2 c[R / 2]; };
+  __device__ __forceinline__ static Raw load_raw(const char* blk, int S, int cb) {
+    Raw w;
     const double2* p = reinterpret_cast<const double2*>(blk);
 #pragma unroll
-    for (int k = 0; k < R / 2; ++k) {
-      double2 v = __ldg(p + (size_t)k * S + cb);
-      u[2 * k] = v.x;
-      u[2 * k + 1] = v.y;
-    }
+    for (int k = 0; k < R / 2; ++k) w.c[k] = __ldg(p + (size_t)k * S + cb);
+    return w;
+  }
+  __device__ __forceinline__ static void decode(const Raw& w, double* u) {
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) { u[2 * k] = w.c[k].x; u[2 * k + 1] = w.c[k].y; }
+  }
+  __device__ __forceinline__ static void load(const char* blk, int S, int cb, double* u) {
+    decode(load_raw(blk, S, cb), u);
   }
   __device__ __forceinline__ static void store(char* blk, int S, int cb, const double* u) {
     double2* p = reinterpret_cast<double2*>(blk);
@@ -108,16 +117,24 @@ template <> struct LinkT<LQ_F32, 18> {
   using real = float;
   static constexpr int NREAL = 18;
   static constexpr size_t bytes_per_site = 72;
-  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+  struct Raw { float4 a[4]; float2 b; };
+  __device__ __forceinline__ static Raw load_raw(const char* blk, int S, int cb) {
+    Raw w;
     const float4* p4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
+    for (int k = 0; k < 4; ++k) w.a[k] = __ldg(p4 + (size_t)k * S + cb);
+    w.b = __ldg(reinterpret_cast<const float2*>(blk + (size_t)S * 64) + cb);
+    return w;
+  }
+  __device__ __forceinline__ static void decode(const Raw& w, float* u) {
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      float4 v = __ldg(p4 + (size_t)k * S + cb);
-      u[4 * k] = v.x; u[4 * k + 1] = v.y; u[4 * k + 2] = v.z; u[4 * k + 3] = v.w;
+      u[4 * k] = w.a[k].x; u[4 * k + 1] = w.a[k].y; u[4 * k + 2] = w.a[k].z; u[4 * k + 3] = w.a[k].w;
     }
-    const float2* p2 = reinterpret_cast<const float2*>(blk + (size_t)S * 64);
-    float2 v = __ldg(p2 + cb);
-    u[16] = v.x; u[17] = v.y;
+    u[16] = w.b.x; u[17] = w.b.y;
+  }
+  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+    decode(load_raw(blk, S, cb), u);
   }
   __device__ __forceinline__ static void store(char* blk, int S, int cb, const double* u) {
     float4* p4 = reinterpret_cast<float4*>(blk);
@@ -134,13 +151,22 @@ template <> struct LinkT<LQ_F32, 12> {
   using real = float;
   static constexpr int NREAL = 12;
   static constexpr size_t bytes_per_site = 48;
-  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+  struct Raw { float4 a[3]; };
+  __device__ __forceinline__ static Raw load_raw(const char* blk, int S, int cb) {
+    Raw w;
     const float4* p4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
+    for (int k = 0; k < 3; ++k) w.a[k] = __ldg(p4 + (size_t)k * S + cb);
+    return w;
+  }
+  __device__ __forceinline__ static void decode(const Raw& w, float* u) {
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float4 v = __ldg(p4 + (size_t)k * S + cb);
-      u[4 * k] = v.x; u[4 * k + 1] = v.y; u[4 * k + 2] = v.z; u[4 * k + 3] = v.w;
+      u[4 * k] = w.a[k].x; u[4 * k + 1] = w.a[k].y; u[4 * k + 2] = w.a[k].z; u[4 * k + 3] = w.a[k].w;
     }
+  }
+  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+    decode(load_raw(blk, S, cb), u);
   }
   __device__ __forceinline__ static void store(char* blk, int S, int cb, const double* u) {
     float4* p4 = reinterpret_cast<float4*>(blk);
@@ -190,19 +216,28 @@ template <lq_prec P> struct Link16<P, 18> {
   using real = float;
   static constexpr int NREAL = 18;
   static constexpr size_t bytes_per_site = 36;
-  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+  struct Raw { uint4 a[2]; uint32_t b; };
+  __device__ __forceinline__ static Raw load_raw(const char* blk, int S, int cb) {
+    Raw w;
     const uint4* p = reinterpret_cast<const uint4*>(blk);
 #pragma unroll
+    for (int k = 0; k < 2; ++k) w.a[k] = __ldg(p + (size_t)k * S + cb);
+    w.b = __ldg(reinterpret_cast<const uint32_t*>(blk + (size_t)S * 32) + cb);
+    return w;
+  }
+  __device__ __forceinline__ static void decode(const Raw& w, float* u) {
+#pragma unroll
     for (int k = 0; k < 2; ++k) {
-      uint4 w = __ldg(p + (size_t)k * S + cb);
-      float2 a = Half16<P>::to_f2(w.x), b = Half16<P>::to_f2(w.y);
-      float2 c = Half16<P>::to_f2(w.z), d = Half16<P>::to_f2(w.w);
+      float2 a = Half16<P>::to_f2(w.a[k].x), b = Half16<P>::to_f2(w.a[k].y);
+      float2 c = Half16<P>::to_f2(w.a[k].z), d = Half16<P>::to_f2(w.a[k].w);
       u[8 * k + 0] = a.x; u[8 * k + 1] = a.y; u[8 * k + 2] = b.x; u[8 * k + 3] = b.y;
       u[8 * k + 4] = c.x; u[8 * k + 5] = c.y; u[8 * k + 6] = d.x; u[8 * k + 7] = d.y;
     }
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(blk + (size_t)S * 32);
-    float2 e = Half16<P>::to_f2(__ldg(q + cb));
+    float2 e = Half16<P>::to_f2(w.b);
     u[16] = e.x; u[17] = e.y;
+  }
+  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+    decode(load_raw(blk, S, cb), u);
   }
   __device__ __forceinline__ static void store(char* blk, int S, int cb, const double* u) {
     uint4* p = reinterpret_cast<uint4*>(blk);
@@ -221,16 +256,22 @@ template <lq_prec P> struct Link16<P, 12> {
   using real = float;
   static constexpr int NREAL = 12;
   static constexpr size_t bytes_per_site = 24;
-  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
-    const uint4* p = reinterpret_cast<const uint4*>(blk);
-    uint4 w = __ldg(p + cb);
-    float2 a = Half16<P>::to_f2(w.x), b = Half16<P>::to_f2(w.y);
-    float2 c = Half16<P>::to_f2(w.z), d = Half16<P>::to_f2(w.w);
+  struct Raw { uint4 a; uint2 b; };
+  __device__ __forceinline__ static Raw load_raw(const char* blk, int S, int cb) {
+    Raw w;
+    w.a = __ldg(reinterpret_cast<const uint4*>(blk) + cb);
+    w.b = __ldg(reinterpret_cast<const uint2*>(blk + (size_t)S * 16) + cb);
+    return w;
+  }
+  __device__ __forceinline__ static void decode(const Raw& w, float* u) {
+    float2 a = Half16<P>::to_f2(w.a.x), b = Half16<P>::to_f2(w.a.y);
+    float2 c = Half16<P>::to_f2(w.a.z), d = Half16<P>::to_f2(w.a.w);
     u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y; u[4] = c.x; u[5] = c.y; u[6] = d.x; u[7] = d.y;
-    const uint2* q = reinterpret_cast<const uint2*>(blk + (size_t)S * 16);
-    uint2 z = __ldg(q + cb);
-    float2 e = Half16<P>::to_f2(z.x), f = Half16<P>::to_f2(z.y);
+    float2 e = Half16<P>::to_f2(w.b.x), f = Half16<P>::to_f2(w.b.y);
     u[8] = e.x; u[9] = e.y; u[10] = f.x; u[11] = f.y;
+  }
+  __device__ __forceinline__ static void load(const char* blk, int S, int cb, float* u) {
+    decode(load_raw(blk, S, cb), u);
   }
   __device__ __forceinline__ static void store(char* blk, int S, int cb, const double* u) {
     uint4* p = reinterpret_cast<uint4*>(blk);

@@ -27,8 +27,8 @@ inline bool stream_capturing(cudaStream_t s) {
   return st != cudaStreamCaptureStatusNone;
 }
 
-// Picks the fastest of `cands` for `key` by timing run(cand) on stream s and caches the
-// choice in the context.  Each candidate is timed as the best of three single launches,
+// Picks a launch shape from `cands` for `key` by timing run(cand) on stream s and caches
+// the choice in the context.  Each candidate is timed as the best of three single launches,
 // each preceded by a write of a buffer twice the L2 size, so that the ranking holds for
 // operands that come from HBM (the regime of large lattices and of streams of different
 // fields) rather than for operands the previous launch left in L2.  Without tuning, or
@@ -53,8 +53,8 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
   cudaEvent_t e0, e1;
   LQ_CUDA(ctx, cudaEventCreate(&e0));
   LQ_CUDA(ctx, cudaEventCreate(&e1));
-  TuneEntry best;
-  best.us = 1e30f;
+  std::vector<TuneEntry> timed;
+  float best_us = 1e30f;
   lq_status st = LQ_OK;
   for (const TuneEntry& c : cands) {
     st = run(c);  // warm-up (first launch of an instance loads its code)
@@ -72,11 +72,29 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
       if (ms * 1000.f < us_best) us_best = ms * 1000.f;
     }
     if (st) break;
-    if (us_best < best.us) { best = c; best.us = us_best; }
+    TuneEntry t = c;
+    t.us = us_best;
+    timed.push_back(t);
+    if (us_best < best_us) best_us = us_best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
+  // Among the shapes close to the fastest lone launch -- within 3% (timing noise) in the
+  // default mode, within 15% in the throughput mode (several independent launches in
+  // flight fill the GPU, so a launch's own parallelism matters less than its instruction
+  // count) -- take the one doing the least redundant work: fewest threads per site, most
+  // right-hand sides per thread, then the candidate order.
+  const float tol = ctx->tune_mode == 2 ? 1.15f : 1.03f;
+  TuneEntry best;
+  bool have = false;
+  for (const TuneEntry& t : timed) {
+    if (t.us > tol * best_us) continue;
+    if (!have || t.tps < best.tps || (t.tps == best.tps && t.rhs_tile > best.rhs_tile)) {
+      best = t;
+      have = true;
+    }
+  }
   ctx->tune[key] = best;
   *pick = best;
   return LQ_OK;
