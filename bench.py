@@ -55,10 +55,11 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def site_bytes(prec, recon, vec):
-    """Algorithmic bytes per output site of a half Dslash: 8 links read once, the input
-    vector read once (its 8-fold neighbour reuse served on chip), the output written once."""
-    return 8 * recon * BYTES[prec] + 2 * 6 * BYTES[vec]
+def site_bytes(prec, recon, vec, nrhs=1):
+    """Algorithmic bytes per output site of a half Dslash: 8 links read once (shared by all
+    right-hand sides), each input vector read once (its 8-fold neighbour reuse served on
+    chip), each output written once."""
+    return 8 * recon * BYTES[prec] + nrhs * 2 * 6 * BYTES[vec]
 
 
 def parse():
@@ -70,6 +71,9 @@ def parse():
     p.add_argument("--prec", default="f32", choices=["f64", "f32", "bf16", "f16"])
     p.add_argument("--recon", type=int, default=18, choices=[18, 12])
     p.add_argument("--vec", default=None, help="vector storage (default: f64 for f64 links, else f32)")
+    p.add_argument("--lattice", default="16,16,16,32", help="Lx,Ly,Lz,Lt of the Dslash workload")
+    p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per Dslash launch")
+    p.add_argument("--field", default="near_identity", choices=["near_identity", "haar"])
     p.add_argument("--streams", type=int, default=4,
                    help="independent applications in flight (graph branches)")
     p.add_argument("--no-variants", action="store_true")
@@ -163,24 +167,24 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ GPU arm -----------
 
-def make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2):
+def make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2, nrhs=1):
     import torch
     import synth
     Vh = synth.volume(dims) // 2
-    chi = synth.fermion_field(dims, 1, seed=seed)
+    chi = synth.fermion_field(dims, nrhs, seed=seed)
     gauges = [lq.lq_gauge_pack(ctx, dims, U_dev, prec, recon) for _ in range(K)]
     host = torch.from_numpy(chi)
 
     def vec_tensor(src=None):
         if vec == "f64":
-            return (src.cuda() if src is not None else torch.empty((1, Vh, 3), dtype=torch.complex128, device="cuda"))
+            return (src.cuda() if src is not None else torch.empty((nrhs, Vh, 3), dtype=torch.complex128, device="cuda"))
         if vec == "f32":
             return (src.to(torch.complex64).cuda() if src is not None
-                    else torch.empty((1, Vh, 3), dtype=torch.complex64, device="cuda"))
+                    else torch.empty((nrhs, Vh, 3), dtype=torch.complex64, device="cuda"))
         dt = torch.bfloat16 if vec == "bf16" else torch.float16
         if src is not None:
             return torch.view_as_real(src).to(dt).contiguous().cuda()
-        return torch.empty((1, Vh, 3, 2), dtype=dt, device="cuda")
+        return torch.empty((nrhs, Vh, 3, 2), dtype=dt, device="cuda")
 
     ins = [vec_tensor(host) for _ in range(K)]
     ts = [vec_tensor() for _ in range(K)]
@@ -196,7 +200,7 @@ def ring_size(bytes_per_copy, l2_bytes, nstreams=4):
     return -(-k // m) * m
 
 
-def run_step(lq, ctx, gauges, ins, ts, outs, vec_code, streams, apps=APPS):
+def run_step(lq, ctx, gauges, ins, ts, outs, vec_code, streams, apps=APPS, nrhs=1):
     """One step: `apps` applications of D.  Application a runs on streams[a % S] (the
     applications are independent; the two halves of one are ordered on its stream), and
     half-Dslash launch h uses ring copy h mod K.  Returns the number of launches."""
@@ -207,8 +211,8 @@ def run_step(lq, ctx, gauges, ins, ts, outs, vec_code, streams, apps=APPS):
         s = streams[a % S]
         c = h % K
         c2 = (h + 1) % K
-        lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, 1, vec_code, s)      # t = D_oe chi
-        lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, 1, vec_code, s)    # out = D_eo t
+        lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, vec_code, s)      # t = D_oe chi
+        lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, vec_code, s)    # out = D_eo t
         h += 2
     return 2 * apps
 
@@ -312,6 +316,41 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
                                        "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
                                        "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
         del gauges, ins, ts, outs
+        torch.cuda.empty_cache()
+    # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
+    for prec in ("f32", "bf16"):
+        vec = "f32" if prec == "f32" else "bf16"
+        sb = 2 * 8 * 18 * BYTES[prec] + 12 * BYTES[vec]
+        K = ring_size(Vh * sb, l2, nstreams)
+        Ld = torch.empty_like(U_dev)
+        lq.lq_long_links(ctx, DIMS, U_dev, -1.0 / 24, Ld)
+        fats = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, 18) for _ in range(K)]
+        lngs = [lq.lq_gauge_pack(ctx, DIMS, Ld, prec, 18) for _ in range(K)]
+        del Ld
+        _, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 12, vec, 1)
+        ins, ts, outs = ins * K, [ts[0]] * K, [outs[0]] * K
+        vc = lq.PREC[vec]
+
+        def istep(ss, fats=fats, lngs=lngs, ins=ins, vc=vc):
+            h = 0
+            for a in range(20):
+                s_ = ss[a % len(ss)]
+                c, c2 = h % K, (h + 1) % K
+                lq.dslash_eo_improved(ctx, fats[c], lngs[c], ins[c], itmp[a % len(ss)], 1, 1, vc, s_)
+                lq.dslash_eo_improved(ctx, fats[c2], lngs[c2], itmp[a % len(ss)], iout[a % len(ss)], 0, 1, vc, s_)
+                h += 2
+            return 40
+        itmp = [torch.empty_like(ins[0]) for _ in range(nstreams)]
+        iout = [torch.empty_like(ins[0]) for _ in range(nstreams)]
+        g = GraphStep(torch, istep, nstreams)
+        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+        del g
+        us = ms * 1000.0 / launches
+        gbs = Vh * sb / us / 1e3
+        out[f"improved/{prec}/18/{vec}"] = {"gflops": round(Vh * 1146 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                            "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
+                                            "bytes_per_site": sb, "ring": K}
+        del fats, lngs, ins, ts, outs, itmp, iout
         torch.cuda.empty_cache()
     # multi-RHS Dslash (links loaded once per site for all right-hand sides)
     import synth
@@ -522,23 +561,25 @@ def run_ours(args):
     vc = lq.PREC[vec]
     props = torch.cuda.get_device_properties(local)
     l2 = int(getattr(props, "L2_cache_size", 128 << 20))
-    Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
-    sb = site_bytes(prec, recon, vec)
+    dims = tuple(int(v) for v in args.lattice.split(","))
+    nrhs = args.nrhs
+    Vh = synth.volume(dims) // 2
+    sb = site_bytes(prec, recon, vec, nrhs)
     K = ring_size(Vh * sb, l2, args.streams)
-    U_host = synth.gauge_field(DIMS, "near_identity", seed=3 + rank, eps=0.3)
+    U_host = synth.gauge_field(dims, args.field, seed=3 + rank, eps=0.3)
     U_dev = torch.from_numpy(U_host).cuda()
-    gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K, seed=2 + rank)
+    gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2 + rank, nrhs=nrhs)
 
     # ---- device-resident throughput
-    step = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss), args.streams)
+    step = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, nrhs=nrhs), args.streams)
     sampler = ClockSampler(local)
     ms, launches, clocks = time_steps(torch, step, args.steps, args.warmup, stream, dist, device, sampler)
-    flops = args.steps * APPS * 2 * Vh * FLOPS_PER_SITE * world
+    flops = args.steps * APPS * 2 * Vh * nrhs * FLOPS_PER_SITE * world
     value = flops / (ms * 1e-3) / 1e9
     us_per_launch = ms * 1000.0 / launches
     achieved = Vh * sb / us_per_launch / 1e3  # GB/s
     peak, peak_kind = measured_peak()
-    key = f"{prec}/{recon}/{vec}"
+    key = f"{prec}/{recon}/{vec}/{'x'.join(map(str, dims))}/{nrhs}"
     traffic = None
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_hash():
         traffic = NCU_TRAFFIC[key][0]
@@ -559,12 +600,14 @@ def run_ours(args):
 
     e2e_steps = max(1, args.steps // 2)
     ms_e2e, _, _ = time_steps(torch, e2e_step, e2e_steps, min(args.warmup, 3), stream, dist, device)
-    e2e_val = e2e_steps * APPS * 2 * Vh * FLOPS_PER_SITE * world / (ms_e2e * 1e-3) / 1e9
+    e2e_val = e2e_steps * APPS * 2 * Vh * nrhs * FLOPS_PER_SITE * world / (ms_e2e * 1e-3) / 1e9
     vbytes = ins[0].numel() * ins[0].element_size()
 
     extra = {}
     if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
-        extra["variants"] = run_variants(lq, ctx, torch, U_dev, l2, stream, args.streams)
+        U_var = U_dev if dims == DIMS else torch.from_numpy(
+            synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)).cuda()
+        extra["variants"] = run_variants(lq, ctx, torch, U_var, l2, stream, args.streams)
     if rank == 0 and not args.no_cg:
         ctx.set_tuning(1)  # the solvers issue one launch at a time
         extra["cg"] = run_cg(lq, ctx, torch, args.cg_maxiter)
@@ -584,9 +627,11 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if prec == "f64" else "f32",
         "data": "synthetic",
-        "config": {"workload": "staggered Dslash, 16^3x32 lattice, links exp(i*0.3*H) on SU(3), "
-                               f"{APPS} full-D applications per step",
-                   "lattice": "16x16x16x32", "link_storage": f"{prec}/{recon}-real", "vector_storage": vec,
+        "config": {"workload": f"staggered Dslash, {'x'.join(map(str, dims))} lattice, "
+                               + ("links exp(i*0.3*H) on SU(3), " if args.field == "near_identity" else "Haar links, ")
+                               + f"{APPS} full-D applications per step" + (f", {nrhs} right-hand sides" if nrhs > 1 else ""),
+                   "lattice": "x".join(map(str, dims)), "nrhs": nrhs,
+                   "link_storage": f"{prec}/{recon}-real", "vector_storage": vec,
                    "l2": f"inputs larger than L2: ring of {K} device copies of links and vectors "
                          f"({K * Vh * sb / 1e6:.0f} MB) cycled across launches",
                    "parallelism": f"replicas x{world}"},
@@ -602,8 +647,8 @@ def run_ours(args):
     }
     line["config"]["streams"] = args.streams
     line["config"]["tuning"] = "autotuned, throughput mode (lq_set_tuning 2)"
-    line["config"]["launch_shape"] = [l for l in ctx.tune_report().splitlines()
-                                      if f"g={prec}/{recon} v={vec} dims=16x16x16x32 nrhs=1" in l]
+    dkey = f"g={prec}/{recon} v={vec} dims={'x'.join(map(str, dims))} nrhs={nrhs}"
+    line["config"]["launch_shape"] = [l for l in ctx.tune_report().splitlines() if dkey in l]
     line.update(extra)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(DIMS)

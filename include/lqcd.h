@@ -123,6 +123,20 @@ lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, 
 lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* c,
                            int64_t n, int adj, lq_prec prec, lq_stream stream);
 
+/* C[i] = A[i] + s B[i] (Table 1: scalar_mult_add_su3_matrix), e.g. the momentum update
+ * P <- P + s F of a molecular-dynamics step.  A, B, C: device complex [n][3][3] of `prec`
+ * (LQ_F64 or LQ_F32); C may be A or B. */
+lq_status su3_scalar_mult_add_batch(lq_context* ctx, const void* A, const void* B, void* C, double s,
+                                    int64_t n, lq_prec prec, lq_stream stream);
+
+/* out[i] = reunit(exp(eps P[i]) U[i]) for traceless anti-Hermitian P (the link update of a
+ * molecular-dynamics step; the paper does not write it down).  exp by scaling and
+ * squaring of a Taylor polynomial (degree 12 in FP64, 7 in FP32, argument scaled to a
+ * row-sum norm <= 1/4); reunit orthonormalises rows 0, 1 and sets row 2 = conj(r0 x r1).
+ * P, U, out: device complex [n][3][3] of `prec` (LQ_F64 or LQ_F32); out may be U. */
+lq_status su3_exp_mul_batch(lq_context* ctx, const void* P, const void* U, void* out, double eps,
+                            int64_t n, lq_prec prec, lq_stream stream);
+
 /* ------------------------------------------------------------------ Dslash ---------- */
 
 /* Half Dslash: out = D in restricted to the sites of parity `out_parity`, `in` living on
@@ -148,6 +162,24 @@ lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* ou
 lq_status dslash_eo_multi(lq_context* ctx, int nlat, const lq_gauge* const* U, const void* const* in,
                           void* const* out, int out_parity, int nrhs, lq_prec vec_prec,
                           lq_stream stream);
+
+/* Improved staggered half Dslash with one-hop ("fat") links F and three-hop ("long",
+ * Naik) links L -- the operator of the improved staggered application the paper times
+ * (Table 4; the paper does not write it down):
+ *   out(x) = sum_mu eta_mu(x) [ F_mu(x) in(x+mu) - F_mu(x-mu)^dag in(x-mu)
+ *                              + L_mu(x) in(x+3mu) - L_mu(x-3mu)^dag in(x-3mu) ]
+ * 1146 flops per output site and rhs.  fat, lng: lq_gauge objects of one lattice packed
+ * with recon 18 and the same precision (fat links are not unitary, long links carry their
+ * coefficient; the smearing that makes F is the caller's).  in, out, nrhs, vec_prec: as
+ * for dslash_eo. */
+lq_status dslash_eo_improved(lq_context* ctx, const lq_gauge* fat, const lq_gauge* lng, const void* in,
+                             void* out, int out_parity, int nrhs, lq_prec vec_prec, lq_stream stream);
+
+/* Naik links L_mu(x) = coeff * U_mu(x) U_mu(x+mu) U_mu(x+2mu) (two mult_su3_nn per link,
+ * Table 1), FP64.  U_canon, L_canon: device complex128 [4][V][3][3] (must not overlap).
+ * Pack L with lq_gauge_pack(..., LQ_RECON_18, ...) for dslash_eo_improved. */
+lq_status lq_long_links(lq_context* ctx, const int dims[4], const void* U_canon, double coeff,
+                        void* L_canon, lq_stream stream);
 
 /* ---------------------------------------------------------------------- CG ---------- */
 

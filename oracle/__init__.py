@@ -15,8 +15,10 @@ Modules
   dslash     stencil and dense staggered D, even/odd blocks, normal operator m^2 - D^2
   cg         FP64 conjugate gradient and the mixed-precision reliable-update CG
   force      action S = Re chi^dag (m^2 - D^2) chi, dS/dchi, dS/dU and its TA projection
+  improved   improved staggered Dslash (one-hop fat + three-hop Naik links), long-link builder
+  md         molecular-dynamics link and momentum updates (exp, reunitarisation, leapfrog)
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than itself
 (brute force, closed forms, invariants, finite differences); see ``tests/test_oracle_*.py``.
 """
-from . import geometry, su3, precision, dslash, cg, force  # noqa: F401
+from . import geometry, su3, precision, dslash, cg, force, improved, md  # noqa: F401

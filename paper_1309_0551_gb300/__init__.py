@@ -78,6 +78,10 @@ def load(path: str | None = None):
                               ctypes.POINTER(lq_cg_stats), P], I),
         "dslash_force": ([P, P, D, P, P, P, P, ctypes.POINTER(D), P], I),
         "dslash_eo_multi": ([P, I, P, P, P, I, I, I, P], I),
+        "dslash_eo_improved": ([P, P, P, P, P, I, I, I, P], I),
+        "lq_long_links": ([P, ctypes.POINTER(I), P, D, P, P], I),
+        "su3_scalar_mult_add_batch": ([P, P, P, P, D, L, I, P], I),
+        "su3_exp_mul_batch": ([P, P, P, P, D, L, I, P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -192,6 +196,20 @@ def dslash_eo(ctx: Context, U: Gauge, inp, out, out_parity: int, nrhs: int = 1, 
                                 int(nrhs), int(vp), _stream(stream)))
 
 
+def dslash_eo_improved(ctx: Context, fat: Gauge, lng: Gauge, inp, out, out_parity: int, nrhs: int = 1,
+                       vec_prec=None, stream=None):
+    """Improved staggered half Dslash (fat one-hop + Naik three-hop links)."""
+    vp = vec_prec_of(inp) if vec_prec is None else vec_prec
+    ctx.check(ctx.lib.dslash_eo_improved(ctx.handle, fat.handle, lng.handle, _ptr(inp), _ptr(out),
+                                         int(out_parity), int(nrhs), int(vp), _stream(stream)))
+
+
+def lq_long_links(ctx: Context, dims, U, coeff: float, L, stream=None):
+    """L_mu(x) = coeff * U_mu(x) U_mu(x+mu) U_mu(x+2mu) (canonical complex128 tensors)."""
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    ctx.check(ctx.lib.lq_long_links(ctx.handle, d, _ptr(U), float(coeff), _ptr(L), _stream(stream)))
+
+
 def dslash_eo_multi(ctx: Context, Us, ins, outs, out_parity: int, nrhs: int = 1, vec_prec=None,
                     stream=None):
     """The half Dslash on several lattices in one persistent launch (lists, one per lattice)."""
@@ -210,6 +228,22 @@ def su3_mul_batch(ctx: Context, A, B, C, n=None, adjA=0, adjB=0, prec=None, stre
     prec = vec_prec_of(A) if prec is None else prec
     ctx.check(ctx.lib.su3_mul_batch(ctx.handle, _ptr(A), _ptr(B), _ptr(C), int(n), int(adjA),
                                     int(adjB), int(prec), _stream(stream)))
+
+
+def su3_scalar_mult_add_batch(ctx: Context, A, B, C, s: float, n=None, prec=None, stream=None):
+    """C = A + s B per 3x3 matrix (Table 1: scalar_mult_add_su3_matrix)."""
+    n = A.numel() // 9 if n is None else n
+    prec = vec_prec_of(A) if prec is None else prec
+    ctx.check(ctx.lib.su3_scalar_mult_add_batch(ctx.handle, _ptr(A), _ptr(B), _ptr(C), float(s), int(n),
+                                                int(prec), _stream(stream)))
+
+
+def su3_exp_mul_batch(ctx: Context, P, U, out, eps: float, n=None, prec=None, stream=None):
+    """out = reunit(exp(eps P) U) per link (P traceless anti-Hermitian)."""
+    n = U.numel() // 9 if n is None else n
+    prec = vec_prec_of(U) if prec is None else prec
+    ctx.check(ctx.lib.su3_exp_mul_batch(ctx.handle, _ptr(P), _ptr(U), _ptr(out), float(eps), int(n),
+                                        int(prec), _stream(stream)))
 
 
 def su3_matvec_batch(ctx: Context, A, b, c, n=None, adj=0, prec=None, stream=None):
@@ -287,3 +321,29 @@ def dslash_force(ctx: Context, U: Gauge, mass: float, chi, dSdU=None, force_TA=N
                                    _ptr(force_TA), _ptr(dSdchi), ctypes.byref(S) if want_S else None,
                                    _stream(stream)))
     return S.value if want_S else None
+
+
+def md_leapfrog(ctx: Context, dims, U, P, chi, mass: float, eps: float, nsteps: int, stream=None):
+    """Leapfrog molecular dynamics for H = -1/2 sum Tr(P^2) + Re chi^dag (m^2 - D^2) chi with
+    chi held fixed: P += eps/2 F; (U = reunit(exp(eps P) U); P += eps F) ..., the last momentum
+    half step eps/2.  U, P: canonical complex128 CUDA tensors (4, V, 3, 3), updated in place;
+    chi: (Vh, 3) complex128.  Every step runs in the library's kernels (dslash_force,
+    su3_exp_mul_batch, su3_scalar_mult_add_batch).  Returns the final action S."""
+    import torch
+    n = U.numel() // 9
+    F = torch.empty_like(U)
+
+    def force():
+        g = lq_gauge_pack(ctx, dims, U, LQ_F64, 18, stream)
+        S = dslash_force(ctx, g, mass, chi, force_TA=F, want_S=True, stream=stream)
+        g.free()
+        return S
+
+    force()
+    su3_scalar_mult_add_batch(ctx, P, F, P, 0.5 * eps, n, LQ_F64, stream)
+    S = None
+    for k in range(nsteps):
+        su3_exp_mul_batch(ctx, P, U, U, eps, n, LQ_F64, stream)
+        S = force()
+        su3_scalar_mult_add_batch(ctx, P, F, P, eps if k < nsteps - 1 else 0.5 * eps, n, LQ_F64, stream)
+    return S

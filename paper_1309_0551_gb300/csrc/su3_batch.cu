@@ -106,6 +106,127 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
   copy_s2g(c + base * 6, sb, cnt * 6);
 }
 
+
+// C = A + s B (scalar_mult_add_su3_matrix, Table 1); C may be A or B (same element).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_su3_axpy(const T* A, const T* B, T* C, T sc, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);
+  T* sB = sA + kThreads * 18;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  copy_g2s(sA, A + base * 18, cnt * 18);
+  copy_g2s(sB, B + base * 18, cnt * 18);
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt * 18; i += blockDim.x) sA[i] = fma(sc, sB[i], sA[i]);
+  __syncthreads();
+  copy_s2g(C + base * 18, sA, cnt * 18);
+}
+
+// 3x3 complex product C = A B on interleaved reals (C must not alias A or B).
+template <class T>
+__device__ __forceinline__ void mat_mul(const T* A, const T* B, T* C) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T re = 0, im = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        re = fma(A[2 * (3 * i + k)], B[2 * (3 * k + j)], re);
+        re = fma(-A[2 * (3 * i + k) + 1], B[2 * (3 * k + j) + 1], re);
+        im = fma(A[2 * (3 * i + k)], B[2 * (3 * k + j) + 1], im);
+        im = fma(A[2 * (3 * i + k) + 1], B[2 * (3 * k + j)], im);
+      }
+      C[2 * (3 * i + j)] = re;
+      C[2 * (3 * i + j) + 1] = im;
+    }
+}
+
+// out = reunit(exp(eps P) U).  exp by scaling and squaring: Y = eps P / 2^s with the
+// row-sum bound of |Y| at most 1/4, exp(Y) by the Taylor polynomial of degree KT in Horner
+// form, then s squarings (truncation below 1e-17 relative in FP64, 1e-9 in FP32).
+// reunit: rows 0 and 1 Gram-Schmidt, row 2 = conj(row0 x row1).
+template <class T, int KT>
+__global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U, T* out, T eps, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sP = reinterpret_cast<T*>(smem_raw);
+  T* sU = sP + kThreads * 18;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  copy_g2s(sP, P + base * 18, cnt * 18);
+  copy_g2s(sU, U + base * 18, cnt * 18);
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    T y[18], e[18], t[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) y[k] = eps * sP[threadIdx.x * 18 + k];
+    T nu = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T rs = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) rs += fabs(y[2 * (3 * i + j)]) + fabs(y[2 * (3 * i + j) + 1]);
+      nu = fmax(nu, rs);
+    }
+    int sq = 0;
+    while (nu > T(0.25) && sq < 60) { nu *= T(0.5); ++sq; }
+    const T scale = ldexp(T(1), -sq);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) y[k] *= scale;
+    // Horner: e = I + y/KT; e = I + (y e)/k for k = KT-1 ... 1
+#pragma unroll
+    for (int k = 0; k < 18; ++k) e[k] = y[k] / T(KT);
+    e[0] += T(1); e[8] += T(1); e[16] += T(1);
+#pragma unroll
+    for (int k = KT - 1; k >= 1; --k) {
+      mat_mul(y, e, t);
+      const T inv = T(1) / T(k);
+#pragma unroll
+      for (int m = 0; m < 18; ++m) e[m] = t[m] * inv;
+      e[0] += T(1); e[8] += T(1); e[16] += T(1);
+    }
+    for (int k = 0; k < sq; ++k) {
+      mat_mul(e, e, t);
+#pragma unroll
+      for (int m = 0; m < 18; ++m) e[m] = t[m];
+    }
+#pragma unroll
+    for (int k = 0; k < 18; ++k) y[k] = sU[threadIdx.x * 18 + k];
+    mat_mul(e, y, t);
+    // reunitarise the rows of t
+    T n0 = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) n0 = fma(t[k], t[k], n0);
+    n0 = T(1) / sqrt(n0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] *= n0;
+    T dr = 0, di = 0;   // <row0, row1> = sum conj(r0_j) r1_j
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dr += t[2 * j] * t[6 + 2 * j] + t[2 * j + 1] * t[6 + 2 * j + 1];
+      di += t[2 * j] * t[6 + 2 * j + 1] - t[2 * j + 1] * t[6 + 2 * j];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T ar = t[2 * j], ai = t[2 * j + 1];
+      t[6 + 2 * j] -= dr * ar - di * ai;
+      t[6 + 2 * j + 1] -= dr * ai + di * ar;
+    }
+    T n1 = 0;
+#pragma unroll
+    for (int k = 6; k < 12; ++k) n1 = fma(t[k], t[k], n1);
+    n1 = T(1) / sqrt(n1);
+#pragma unroll
+    for (int k = 6; k < 12; ++k) t[k] *= n1;
+    reconstruct_row2(t);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) sP[threadIdx.x * 18 + k] = t[k];
+  }
+  __syncthreads();
+  copy_s2g(out + base * 18, sP, cnt * 18);
+}
+
 template <class T>
 cudaError_t launch_mul(const void* A, const void* B, void* C, int64_t n, int adjA, int adjB, cudaStream_t s) {
   const int64_t blocks = (n + kThreads - 1) / kThreads;
@@ -129,13 +250,13 @@ cudaError_t launch_matvec(const void* A, const void* b, void* c, int64_t n, int 
   return cudaGetLastError();
 }
 
-bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+}  // namespace
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
   const char* pb = (const char*)b;
   return pa < pb + nb && pb < pa + na;
 }
-
-}  // namespace
 
 extern "C" lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, int64_t n,
                                    int adjA, int adjB, lq_prec prec, lq_stream stream) {
@@ -171,5 +292,53 @@ extern "C" lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = prec == LQ_F64 ? launch_matvec<double>(A, b, c, n, adj, s) : launch_matvec<float>(A, b, c, n, adj, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_matvec");
+  return LQ_OK;
+}
+
+extern "C" lq_status su3_scalar_mult_add_batch(lq_context* ctx, const void* A, const void* B, void* C, double s,
+                                               int64_t n, lq_prec prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (prec != LQ_F64 && prec != LQ_F32) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "LQ_F64 or LQ_F32 only");
+  if (n == 0) return LQ_OK;
+  if (!A || !B || !C || !lq_aligned16(A) || !lq_aligned16(B) || !lq_aligned16(C))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be non-NULL 16-byte aligned device pointers");
+  const size_t bytes = (size_t)n * 18 * lq_prec_bytes(prec);
+  if ((C != A && overlaps(C, bytes, A, bytes)) || (C != B && overlaps(C, bytes, B, bytes)))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "C must be A, B or disjoint from both");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  if (prec == LQ_F64)
+    k_su3_axpy<double><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(double), st>>>(
+        (const double*)A, (const double*)B, (double*)C, s, n);
+  else
+    k_su3_axpy<float><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(float), st>>>(
+        (const float*)A, (const float*)B, (float*)C, (float)s, n);
+  LQ_CHECK_LAUNCH(ctx, "k_su3_axpy");
+  return LQ_OK;
+}
+
+extern "C" lq_status su3_exp_mul_batch(lq_context* ctx, const void* P, const void* U, void* out, double eps,
+                                       int64_t n, lq_prec prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (prec != LQ_F64 && prec != LQ_F32) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "LQ_F64 or LQ_F32 only");
+  if (n == 0) return LQ_OK;
+  if (!P || !U || !out || !lq_aligned16(P) || !lq_aligned16(U) || !lq_aligned16(out))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be non-NULL 16-byte aligned device pointers");
+  const size_t bytes = (size_t)n * 18 * lq_prec_bytes(prec);
+  if ((out != U && overlaps(out, bytes, U, bytes)) || overlaps(out, bytes, P, bytes))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "out must be U or disjoint from U and P");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  if (prec == LQ_F64)
+    k_su3_exp_mul<double, 12><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(double), st>>>(
+        (const double*)P, (const double*)U, (double*)out, eps, n);
+  else
+    k_su3_exp_mul<float, 7><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(float), st>>>(
+        (const float*)P, (const float*)U, (float*)out, (float)eps, n);
+  LQ_CHECK_LAUNCH(ctx, "k_su3_exp_mul");
   return LQ_OK;
 }

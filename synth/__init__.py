@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "rng", "volume", "check_dims", "complex_gaussian", "haar_su3", "near_identity_su3",
-    "gauge_field", "fermion_field", "su3_pairs",
+    "gauge_field", "fermion_field", "su3_pairs", "momenta",
 ]
 
 _CHUNK = 1 << 18  # matrices generated per batch, bounds host memory for large lattices
@@ -126,3 +126,15 @@ def su3_pairs(n: int, seed: int = 2) -> tuple:
     """``n`` pairs of Haar SU(3) matrices (for the batched SU(3) products)."""
     g = rng(seed)
     return haar_su3(g, n), haar_su3(g, n)
+
+
+def momenta(dims, seed: int = 8, scale: float = 1.0) -> np.ndarray:
+    """Canonical (4, V, 3, 3) field of i*H, H a Gaussian traceless Hermitian 3x3 matrix
+    (anti-Hermitian, traceless), scaled by ``scale``."""
+    V = volume(dims)
+    g = rng(seed)
+    A = complex_gaussian(g, (4 * V, 3, 3))
+    H = 0.5 * (A + np.conj(np.swapaxes(A, -1, -2)))
+    tr = np.trace(H, axis1=-2, axis2=-1).real / 3.0
+    H = H - tr[:, None, None] * np.eye(3)
+    return (1j * scale * H).reshape(4, V, 3, 3)
