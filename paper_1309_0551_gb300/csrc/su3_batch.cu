@@ -2,12 +2,18 @@
 // (su3_mul_batch) and mult_su3_mat_vec / mult_adj_su3_mat_vec (su3_matvec_batch).
 //
 // The operands arrive in the canonical array-of-structures layout (one 3x3 complex matrix
-// = 18 contiguous reals).  A block stages its slice of every operand through shared memory
-// with coalesced 16-byte loads, each thread multiplies one pair from shared memory, and
-// the results leave through shared memory with coalesced 16-byte stores: every byte of
-// global memory is touched once, in full sectors.
+// = 18 contiguous reals).  A block's slice of every operand is one contiguous range: it is
+// brought into shared memory by TMA bulk copies (cp.async.bulk, one thread issues, an
+// mbarrier signals arrival), each thread works on one item from shared memory, and the
+// result slice leaves by a TMA bulk store.  Every byte of global memory is touched once,
+// in full sectors.  Slices whose size is not a multiple of 16 bytes (a ragged last block)
+// use coalesced 16-byte loads and stores by all threads instead.
 #include "lqcd_internal.cuh"
+#include "tma.cuh"
 #include "tune.cuh"
+
+// Blocks that gave up waiting for a bulk copy (should stay 0; see tma.cuh).
+__device__ unsigned int g_su3_tma_timeouts;
 
 namespace {
 
@@ -35,6 +41,50 @@ __device__ __forceinline__ void copy_s2g(T* __restrict__ dst, const T* __restric
   for (int i = nvec * V + threadIdx.x; i < nreal; i += blockDim.x) dst[i] = src[i];
 }
 
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Brings nA reals from gA and nB from gB into shared memory (sA, sB); returns false if the
+// block must skip its work (a bulk copy did not arrive within the wait limit).  Ends with
+// a barrier.
+template <class T>
+__device__ __forceinline__ bool stage_in(T* sA, const T* gA, int nA, T* sB, const T* gB, int nB, uint64_t* bar) {
+  __shared__ int ok;
+  const uint32_t bA = nA * sizeof(T), bB = nB * sizeof(T);
+  if (bA % 16 == 0 && bB % 16 == 0 && aligned16(gA) && aligned16(gB)) {
+    if (threadIdx.x == 0) {
+      tma::mbar_init(bar, 1);
+      tma::mbar_expect_tx(bar, bA + bB);
+      tma::load(sA, gA, bA, bar);
+      tma::load(sB, gB, bB, bar);
+      ok = tma::mbar_wait(bar, 0);
+      if (!ok) atomicAdd(&g_su3_tma_timeouts, 1u);
+    }
+    __syncthreads();
+    return ok != 0;
+  }
+  copy_g2s(sA, gA, nA);
+  copy_g2s(sB, gB, nB);
+  __syncthreads();
+  return true;
+}
+
+// Writes nC reals of shared memory sC to gC (after every thread's writes to sC).
+template <class T>
+__device__ __forceinline__ void stage_out(T* gC, const T* sC, int nC) {
+  const uint32_t bC = nC * sizeof(T);
+  if (bC % 16 == 0 && aligned16(gC)) {
+    tma::fence_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma::store(gC, sC, bC);
+      tma::wait_all();
+    }
+  } else {
+    __syncthreads();
+    copy_s2g(gC, sC, nC);
+  }
+}
+
 // element (i, j) of op(X): X_ij, or conj(X_ji) for the adjoint
 template <int ADJ, class T>
 __device__ __forceinline__ void elem(const T* x, int i, int j, T& re, T& im) {
@@ -46,13 +96,12 @@ template <class T, int ADJA, int ADJB>
 __global__ void __launch_bounds__(kThreads) k_su3_mul(const T* __restrict__ A, const T* __restrict__ B,
                                                       T* __restrict__ C, int64_t n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sB = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  copy_g2s(sA, A + base * 18, cnt * 18);
-  copy_g2s(sB, B + base * 18, cnt * 18);
-  __syncthreads();
+  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar)) return;
   if ((int)threadIdx.x < cnt) {
     T a[18], b[18], c[18];
 #pragma unroll
@@ -76,21 +125,19 @@ __global__ void __launch_bounds__(kThreads) k_su3_mul(const T* __restrict__ A, c
 #pragma unroll
     for (int k = 0; k < 18; ++k) sA[threadIdx.x * 18 + k] = c[k];
   }
-  __syncthreads();
-  copy_s2g(C + base * 18, sA, cnt * 18);
+  stage_out(C + base * 18, sA, cnt * 18);
 }
 
 template <class T, int ADJ>
 __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A, const T* __restrict__ b,
                                                          T* __restrict__ c, int64_t n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sb = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  copy_g2s(sA, A + base * 18, cnt * 18);
-  copy_g2s(sb, b + base * 6, cnt * 6);
-  __syncthreads();
+  if (!stage_in(sA, A + base * 18, cnt * 18, sb, b + base * 6, cnt * 6, &bar)) return;
   if ((int)threadIdx.x < cnt) {
     T a[18], v[6], r[6];
 #pragma unroll
@@ -102,8 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
 #pragma unroll
     for (int k = 0; k < 6; ++k) sb[threadIdx.x * 6 + k] = r[k];
   }
-  __syncthreads();
-  copy_s2g(c + base * 6, sb, cnt * 6);
+  stage_out(c + base * 6, sb, cnt * 6);
 }
 
 
@@ -111,16 +157,14 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_su3_axpy(const T* A, const T* B, T* C, T sc, int64_t n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sB = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  copy_g2s(sA, A + base * 18, cnt * 18);
-  copy_g2s(sB, B + base * 18, cnt * 18);
-  __syncthreads();
+  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar)) return;
   for (int i = threadIdx.x; i < cnt * 18; i += blockDim.x) sA[i] = fma(sc, sB[i], sA[i]);
-  __syncthreads();
-  copy_s2g(C + base * 18, sA, cnt * 18);
+  stage_out(C + base * 18, sA, cnt * 18);
 }
 
 // 3x3 complex product C = A B on interleaved reals (C must not alias A or B).
@@ -150,13 +194,12 @@ __device__ __forceinline__ void mat_mul(const T* A, const T* B, T* C) {
 template <class T, int KT>
 __global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U, T* out, T eps, int64_t n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
   T* sP = reinterpret_cast<T*>(smem_raw);
   T* sU = sP + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  copy_g2s(sP, P + base * 18, cnt * 18);
-  copy_g2s(sU, U + base * 18, cnt * 18);
-  __syncthreads();
+  if (!stage_in(sP, P + base * 18, cnt * 18, sU, U + base * 18, cnt * 18, &bar)) return;
   if ((int)threadIdx.x < cnt) {
     T y[18], e[18], t[18];
 #pragma unroll
@@ -223,8 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U
 #pragma unroll
     for (int k = 0; k < 18; ++k) sP[threadIdx.x * 18 + k] = t[k];
   }
-  __syncthreads();
-  copy_s2g(out + base * 18, sP, cnt * 18);
+  stage_out(out + base * 18, sP, cnt * 18);
 }
 
 template <class T>
