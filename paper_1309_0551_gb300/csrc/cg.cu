@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(kBlas) k_cg_update(void* x, void* r, const voi
   using VT = VecT<VP>;
   using T = typename VT::real;
   const int rhs = blockIdx.y;
+  pdl_trigger();
+  pdl_wait();
   const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state) + rhs;
   const T alpha = (T)sc->alpha;
   double acc[1] = {0.0};
@@ -73,6 +75,8 @@ __global__ void __launch_bounds__(kBlas) k_cg_xpay(const void* r, void* p, const
   using VT = VecT<VP>;
   using T = typename VT::real;
   const int rhs = blockIdx.y;
+  pdl_trigger();
+  pdl_wait();
   if (!sc[rhs].active) return;
   const T beta = (T)sc[rhs].beta;
   const size_t off = (size_t)rhs * Vh;
@@ -92,6 +96,8 @@ __global__ void __launch_bounds__(kBlas) k_convert(const void* src, void* dst, i
   using S = VecT<VS>;
   using D = VecT<VD>;
   const int rhs = blockIdx.y;
+  pdl_trigger();
+  pdl_wait();
   const size_t off = (size_t)rhs * Vh;
   double acc[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
@@ -116,6 +122,8 @@ template <lq_prec VL>
 __global__ void __launch_bounds__(kBlas) k_fold(double* x_hi, void* x_lo, int Vh) {
   using L = VecT<VL>;
   const int rhs = blockIdx.y;
+  pdl_trigger();
+  pdl_wait();
   const size_t off = (size_t)rhs * Vh;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
     typename L::real a[6], z[6];
@@ -308,6 +316,7 @@ struct Solver {
   double* partials;
   unsigned int* counter;
   int nblocks_max;
+  bool pdl = false;      // programmatic dependent launch for the iteration kernels
   int nsys = 0;          // independent systems: nrhs, or nlat * nrhs when batched
   size_t sites = 0;      // sites of one full vector (all systems)
   const Batch* batch = nullptr;
@@ -402,9 +411,12 @@ lq_status launch_blas_update(Solver& S) {
   }
   dim3 grid(S.nbx, S.nrhs);
   Reducer red = S.reducer(FIN_BETA);
-  if (S.vp == LQ_F64) k_cg_update<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.xl, S.r, S.p, S.Ap, S.Vh, red);
-  else k_cg_update<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.xl, S.r, S.p, S.Ap, S.Vh, red);
-  LQ_CHECK_LAUNCH(S.ctx, "k_cg_update");
+  cudaError_t e = S.vp == LQ_F64
+                      ? launch_k(k_cg_update<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
+                                 (const void*)S.Ap, S.Vh, red)
+                      : launch_k(k_cg_update<LQ_F32>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
+                                 (const void*)S.Ap, S.Vh, red);
+  if (e != cudaSuccess) return lq_cuda_fail(S.ctx, e, "k_cg_update");
   return LQ_OK;
 }
 
@@ -417,9 +429,12 @@ lq_status launch_xpay(Solver& S) {
     return LQ_OK;
   }
   dim3 grid(S.nbx, S.nrhs);
-  if (S.vp == LQ_F64) k_cg_xpay<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, S.Vh);
-  else k_cg_xpay<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.r, S.p, S.sc, S.Vh);
-  LQ_CHECK_LAUNCH(S.ctx, "k_cg_xpay");
+  cudaError_t e = S.vp == LQ_F64
+                      ? launch_k(k_cg_xpay<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, (const void*)S.r, S.p,
+                                 (const CGScalars*)S.sc, S.Vh)
+                      : launch_k(k_cg_xpay<LQ_F32>, grid, dim3(kBlas), 0, S.s, S.pdl, (const void*)S.r, S.p,
+                                 (const CGScalars*)S.sc, S.Vh);
+  if (e != cudaSuccess) return lq_cuda_fail(S.ctx, e, "k_cg_xpay");
   return LQ_OK;
 }
 
@@ -440,6 +455,7 @@ lq_status iteration(Solver& S) {
   d.nrhs = S.nrhs;
   d.vec_prec = S.vp;
   d.rhs_stride = S.Vh;
+  d.pdl = S.pdl;
   st = launch_dslash(S.ctx, d, S.s);
   if (st) return st;
   Reducer red = S.reducer(FIN_ALPHA);
@@ -760,6 +776,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.Uhi = U_hi;
   S.Ulo = U_lo ? U_lo : U_hi;
   S.mixed = U_lo != nullptr;
+  S.pdl = true;
   S.vp = S.mixed ? LQ_F32 : LQ_F64;
   S.mass = mass;
   S.nrhs = nrhs;

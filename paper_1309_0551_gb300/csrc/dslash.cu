@@ -85,6 +85,7 @@ static DslashKArgs make_kargs(const DslashArgs& a) {
   k.reduce = a.reduce;
   if (a.red) k.red = *a.red;
   else k.red = Reducer{nullptr, nullptr, nullptr, 0, 0, nullptr};
+  k.pdl = a.pdl ? 1 : 0;
   return k;
 }
 
@@ -95,6 +96,7 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   // Tune on the plain operator (no epilogue, no reduction: repeatable launches), then use
   // the chosen shape for this launch.
   DslashKArgs plain = k;
+  plain.pdl = 0;
   plain.w1 = plain.w2 = nullptr;
   plain.a1 = plain.a2 = 0.0;
   plain.c = 1.0;

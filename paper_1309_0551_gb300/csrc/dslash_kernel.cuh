@@ -26,6 +26,7 @@ struct DslashKArgs {
   double c;
   int reduce;
   Reducer red;
+  int pdl;     // host side only: launch with programmatic dependent launch
 };
 
 // One thread per (output site, direction group), TPS threads per site, NR right-hand sides
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   const int sub = gtid % TPS;
   const int rhs0 = ty * NR;
   const bool live = cb < a.G.Vh;
+  pdl_trigger();
   double part[NR];
   T acc[NR][6];
 #pragma unroll
@@ -52,6 +54,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[r][k] = T(0);
   }
+  pdl_wait();
   if (live)
     dslash_hops<GP, R, VP, NR, TPS>(a.gauge, a.blk_bytes, a.G, a.out_par, a.in, a.rhs_stride, a.nrhs, rhs0,
                                     cb, sub, acc);
@@ -74,8 +77,7 @@ template <lq_prec GP, int R, lq_prec VP, int NR, int TPS>
 static cudaError_t launch_dslash_inst(const DslashKArgs& k, int block, cudaStream_t s) {
   const long long nbx = ((long long)k.G.Vh * TPS + block - 1) / block;
   dim3 grid((unsigned)(nbx * ((k.nrhs + NR - 1) / NR)));
-  k_dslash<GP, R, VP, NR, TPS><<<grid, block, 0, s>>>(k);
-  return cudaGetLastError();
+  return launch_k(k_dslash<GP, R, VP, NR, TPS>, grid, dim3(block), 0, s, k.pdl != 0, k);
 }
 
 template <lq_prec GP, int R, lq_prec VP>

@@ -421,6 +421,31 @@ template <class T> __device__ __forceinline__ void adj_mat_vec_acc(const T* u, c
   }
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialization
+// attribute may start while its predecessor on the stream is still running: it calls
+// pdl_trigger() at once (so that its own successor can be scheduled early too) and
+// pdl_wait() before touching anything an earlier kernel writes or reads.  Both are no-ops
+// for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches `kernel` on `s`, with the programmatic-serialization attribute when `pdl`.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Lattice geometry passed to kernels.
 struct Geom {
   int Lx, Ly, Lz, Lt;
@@ -457,6 +482,7 @@ struct DslashArgs {
   double c = 1.0;
   int reduce = RED_NONE;
   struct Reducer* red = nullptr;
+  bool pdl = false;    // launch with programmatic dependent launch (solver loops)
 };
 
 // Deterministic per-rhs reduction: blocks store partials, the last block to finish sums
