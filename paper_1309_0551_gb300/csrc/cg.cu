@@ -38,56 +38,91 @@ template <class T> __device__ __forceinline__ double site_norm2(const T* v) {
   return (double)s;
 }
 
-// x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs).
+// A vector of one rhs seen as 16-byte chunks (float4 for FP32, double2 for FP64): a
+// site-ordered vector is contiguous and Vh * bytes_per_site is a multiple of 16 (Vh is
+// a multiple of 8), so the BLAS kernels need no site structure and every access is a
+// full-width, fully coalesced 16-byte load or store.
+template <lq_prec VP> struct Chunk;
+template <> struct Chunk<LQ_F32> {
+  using real = float;
+  using vec = float4;
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void get(const vec& a, float* v) { v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; }
+  __device__ __forceinline__ static vec put(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct Chunk<LQ_F64> {
+  using real = double;
+  using vec = double2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void get(const vec& a, double* v) { v[0] = a.x; v[1] = a.y; }
+  __device__ __forceinline__ static vec put(const double* v) { return make_double2(v[0], v[1]); }
+};
+
+// x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), grid-stride over
+// the rhs's 16-byte chunks.  The chunk's squares are summed in the vector precision, the
+// running sum in FP64.  (A TMA-tiled variant -- four bulk loads into shared memory, two
+// bulk stores -- measured slower than the grid-stride form: 21.8 vs 20.1 us FP32, 44 vs
+// 35 us FP64 at 32^4, with the per-site 8-byte accesses the grid-stride form then used.)
 template <lq_prec VP>
 __global__ void __launch_bounds__(kBlas) k_cg_update(void* x, void* r, const void* p, const void* Ap,
                                                      int Vh, Reducer red) {
-  using VT = VecT<VP>;
-  using T = typename VT::real;
+  using C = Chunk<VP>;
+  using T = typename C::real;
+  using V = typename C::vec;
   const int rhs = blockIdx.y;
-  pdl_trigger();
   pdl_wait();
   const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state) + rhs;
   const T alpha = (T)sc->alpha;
   double acc[1] = {0.0};
-  const size_t off = (size_t)rhs * Vh;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
-    T xv[6], rv[6], pv[6], av[6];
-    VT::load_rw(x, off + i, xv);
-    VT::load_rw(r, off + i, rv);
-    VT::load(p, off + i, pv);
-    VT::load(Ap, off + i, av);
+  const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
+  V* xc = reinterpret_cast<V*>(x) + rhs * nch;
+  V* rc = reinterpret_cast<V*>(r) + rhs * nch;
+  const V* pc = reinterpret_cast<const V*>(p) + rhs * nch;
+  const V* ac = reinterpret_cast<const V*>(Ap) + rhs * nch;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+    T xv[C::n], rv[C::n], pv[C::n], av[C::n];
+    C::get(xc[i], xv);
+    C::get(rc[i], rv);
+    C::get(__ldg(pc + i), pv);
+    C::get(__ldg(ac + i), av);
+    T s = 0;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < C::n; ++k) {
       xv[k] = fma(alpha, pv[k], xv[k]);
       rv[k] = fma(-alpha, av[k], rv[k]);
+      s = fma(rv[k], rv[k], s);
     }
-    VT::store(x, off + i, xv);
-    VT::store(r, off + i, rv);
-    acc[0] += site_norm2(rv);
+    xc[i] = C::put(xv);
+    rc[i] = C::put(rv);
+    acc[0] += (double)s;
   }
+  pdl_trigger();
   block_reduce<1>(acc, red, rhs, gridDim.y);
 }
 
-// p = r + beta p for active right-hand sides.  grid = (nbx, nrhs).
+// p = r + beta p for active right-hand sides.  grid = (nbx, nrhs), 16-byte chunks.
 template <lq_prec VP>
 __global__ void __launch_bounds__(kBlas) k_cg_xpay(const void* r, void* p, const CGScalars* sc, int Vh) {
-  using VT = VecT<VP>;
-  using T = typename VT::real;
+  using C = Chunk<VP>;
+  using T = typename C::real;
+  using V = typename C::vec;
   const int rhs = blockIdx.y;
-  pdl_trigger();
   pdl_wait();
-  if (!sc[rhs].active) return;
-  const T beta = (T)sc[rhs].beta;
-  const size_t off = (size_t)rhs * Vh;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
-    T rv[6], pv[6];
-    VT::load(r, off + i, rv);
-    VT::load_rw(p, off + i, pv);
+  if (sc[rhs].active) {
+    const T beta = (T)sc[rhs].beta;
+    const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
+    const V* rc = reinterpret_cast<const V*>(r) + rhs * nch;
+    V* pc = reinterpret_cast<V*>(p) + rhs * nch;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+      T rv[C::n], pv[C::n];
+      C::get(__ldg(rc + i), rv);
+      C::get(pc[i], pv);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) pv[k] = fma(beta, pv[k], rv[k]);
-    VT::store(p, off + i, pv);
+      for (int k = 0; k < C::n; ++k) pv[k] = fma(beta, pv[k], rv[k]);
+      pc[i] = C::put(pv);
+    }
   }
+  pdl_trigger();
 }
 
 // dst (precision VD) = src (precision VS) for every rhs; optional ||dst||^2 -> FIN_STORE.
@@ -96,7 +131,6 @@ __global__ void __launch_bounds__(kBlas) k_convert(const void* src, void* dst, i
   using S = VecT<VS>;
   using D = VecT<VD>;
   const int rhs = blockIdx.y;
-  pdl_trigger();
   pdl_wait();
   const size_t off = (size_t)rhs * Vh;
   double acc[1] = {0.0};
@@ -122,7 +156,6 @@ template <lq_prec VL>
 __global__ void __launch_bounds__(kBlas) k_fold(double* x_hi, void* x_lo, int Vh) {
   using L = VecT<VL>;
   const int rhs = blockIdx.y;
-  pdl_trigger();
   pdl_wait();
   const size_t off = (size_t)rhs * Vh;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {

@@ -93,22 +93,35 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   DslashLaunchFn fn = pick_fn(a.U);
   if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
   DslashKArgs k = make_kargs(a);
-  // Tune on the plain operator (no epilogue, no reduction: repeatable launches), then use
-  // the chosen shape for this launch.
+  // Tuning launches must be repeatable.  A launch without reduction is tuned on the plain
+  // operator; a launch with a reduction is tuned as itself (its cost depends on the number
+  // of blocks it reduces over), which is repeatable because the solvers never let out alias
+  // w1 or w2 and their reductions only store totals or alpha = rr / total.
   DslashKArgs plain = k;
   plain.pdl = 0;
-  plain.w1 = plain.w2 = nullptr;
-  plain.a1 = plain.a2 = 0.0;
-  plain.c = 1.0;
-  plain.reduce = RED_NONE;
+  if (a.reduce == RED_NONE) {
+    plain.w1 = plain.w2 = nullptr;
+    plain.a1 = plain.a2 = 0.0;
+    plain.c = 1.0;
+  }
   TuneEntry pick;
   const TuneEntry& f = ctx->forced;
   if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
       !(a.U->prec == LQ_F64 && f.rhs_tile > 4)) {
     pick = f;
   } else {
+    std::string key = dslash_key(a.U, a.vec_prec, a.nrhs);
+    std::vector<TuneEntry> cands = dslash_candidates(a.U->prec, a.nrhs);
+    if (a.reduce != RED_NONE) {
+      key += a.reduce == RED_DOT ? " red=dot" : " red=norm";
+      std::vector<TuneEntry> fit;  // every candidate must fit the reduction scratch
+      for (const TuneEntry& c : cands)
+        if (a.red && (long long)k.G.Vh * c.tps / c.block + 1 <= a.red->nblocks_max) fit.push_back(c);
+      if (fit.empty()) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
+      cands = fit;
+    }
     lq_status st = tune_pick(
-        ctx, dslash_key(a.U, a.vec_prec, a.nrhs), dslash_candidates(a.U->prec, a.nrhs), s,
+        ctx, key, cands, s,
         [&](const TuneEntry& c) -> lq_status {
           cudaError_t e = fn(plain, a.vec_prec, c.block, c.rhs_tile, c.tps, s);
           if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash (tuning)");

@@ -45,7 +45,6 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   const int sub = gtid % TPS;
   const int rhs0 = ty * NR;
   const bool live = cb < a.G.Vh;
-  pdl_trigger();
   double part[NR];
   T acc[NR][6];
 #pragma unroll
@@ -62,6 +61,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   if (live)
     dslash_epilogue<VP, NR, TPS>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, a.reduce, a.rhs_stride, a.nrhs,
                                  rhs0, cb, sub, part);
+  pdl_trigger();  // this block's main work is done: the successor may be scheduled
   if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 

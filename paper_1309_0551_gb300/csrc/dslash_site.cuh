@@ -107,6 +107,7 @@ __device__ __forceinline__ void dslash_epilogue(const T (&acc)[NR][6], void* out
   for (int r = 0; r < NR; ++r) {
     if (rhs0 + r < nrhs) {
       const size_t site = (size_t)(rhs0 + r) * rhs_stride + cb;
+      T ps = T(0);  // this thread's share of the site's dot or norm, in the vector precision
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (c % TPS != sub) continue;
@@ -125,10 +126,11 @@ __device__ __forceinline__ void dslash_epilogue(const T (&acc)[NR][6], void* out
         }
         VT::store_c(out, site, c, res);
         if (reduce == RED_DOT)
-          part[r] += (double)w[0] * (double)res[0] + (double)w[1] * (double)res[1];
+          ps = fma(w[0], res[0], fma(w[1], res[1], ps));
         else if (reduce == RED_NORM)
-          part[r] += (double)res[0] * (double)res[0] + (double)res[1] * (double)res[1];
+          ps = fma(res[0], res[0], fma(res[1], res[1], ps));
       }
+      part[r] += (double)ps;
     }
   }
 }

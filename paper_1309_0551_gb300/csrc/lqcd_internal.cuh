@@ -422,10 +422,11 @@ template <class T> __device__ __forceinline__ void adj_mat_vec_acc(const T* u, c
 }
 
 // Programmatic dependent launch.  A kernel launched with the programmatic-serialization
-// attribute may start while its predecessor on the stream is still running: it calls
-// pdl_trigger() at once (so that its own successor can be scheduled early too) and
-// pdl_wait() before touching anything an earlier kernel writes or reads.  Both are no-ops
-// for kernels launched without the attribute.
+// attribute may be scheduled while its predecessor on the stream drains: it calls
+// pdl_wait() before touching anything an earlier kernel writes or reads, and pdl_trigger()
+// once its own main work is done (triggering at the start would let the successor's
+// blocks occupy SMs that this kernel's remaining blocks still need).  Both are no-ops for
+// kernels launched without the attribute.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

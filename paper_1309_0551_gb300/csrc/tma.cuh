@@ -51,7 +51,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
 // Make this thread's generic-proxy shared-memory writes visible to the async proxy.
 __device__ __forceinline__ void fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared -> global bulk store, committed as a bulk group; wait_all() waits for completion.
+// Shared -> global bulk store, committed as a bulk group; wait_all() waits until every
+// committed store has finished reading shared memory (the block may then exit or reuse it;
+// the global writes complete on their own, before the kernel is complete).
 __device__ __forceinline__ void store(void* dst, const void* src_smem, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem(src_smem)),
                "r"(bytes)
@@ -59,6 +61,6 @@ __device__ __forceinline__ void store(void* dst, const void* src_smem, uint32_t 
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void wait_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 }  // namespace tma

@@ -28,11 +28,12 @@ inline bool stream_capturing(cudaStream_t s) {
 }
 
 // Picks a launch shape from `cands` for `key` by timing run(cand) on stream s and caches
-// the choice in the context.  Each candidate is timed as the best of three single launches,
-// each preceded by a write of a buffer twice the L2 size, so that the ranking holds for
-// operands that come from HBM (the regime of large lattices and of streams of different
-// fields) rather than for operands the previous launch left in L2.  Without tuning, or
+// the choice in the context.  Each candidate is timed as kTuneBurst back-to-back launches
+// (per-launch average, best of three repetitions), each burst preceded by a write of a
+// buffer twice the L2 size: the first launch finds nothing in L2 and the following ones
+// run the way a solver or a graph issues them, one after another.  Without tuning, or
 // while the stream is being captured, the first candidate is used and nothing is cached.
+constexpr int kTuneBurst = 3;
 template <class F>
 lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<TuneEntry>& cands,
                     cudaStream_t s, F run, TuneEntry* pick) {
@@ -63,13 +64,14 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
     for (int rep = 0; rep < 3; ++rep) {
       cudaMemsetAsync(ctx->flush, rep, ctx->flush_bytes, s);
       cudaEventRecord(e0, s);
-      run(c);
+      for (int k = 0; k < kTuneBurst; ++k) run(c);
       cudaEventRecord(e1, s);
       cudaError_t err = cudaEventSynchronize(e1);
       if (err != cudaSuccess) { st = lq_cuda_fail(ctx, err, "tune"); break; }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms * 1000.f < us_best) us_best = ms * 1000.f;
+      const float us = ms * 1000.f / kTuneBurst;
+      if (us < us_best) us_best = us;
     }
     if (st) break;
     TuneEntry t = c;
@@ -171,9 +173,10 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
       if (lane == 0 && rhs0 + r < nrhs) red.partials[(size_t)(rhs0 + r) * nbx + bx] = x;
     }
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    // thread 0 wrote this block's partials: make them visible before counting the block
+    __threadfence();
     unsigned total = gridDim.x * gridDim.y;
     unsigned prev = atomicAdd(red.counter, 1u);
     am_last = (prev == total - 1);
@@ -181,11 +184,19 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  for (int rhs = warp; rhs < nrhs; rhs += nw) {
+  // the whole block sums each row (strided by thread, then a fixed tree): deterministic
+  for (int rhs = 0; rhs < nrhs; ++rhs) {
     double x = 0.0;
-    for (int b = lane; b < nbx; b += 32) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
+    for (int b = threadIdx.x; b < nbx; b += blockDim.x) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
     x = warp_sum(x);
-    if (lane == 0) finish_one(red, rhs, x);
+    __syncthreads();                       // sm[0][] free again
+    if (lane == 0) sm[0][warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      double y = lane < nw ? sm[0][lane] : 0.0;
+      y = warp_sum(y);
+      if (lane == 0) finish_one(red, rhs, y);
+    }
   }
   if (threadIdx.x == 0) *red.counter = 0u;
 }
@@ -225,9 +236,10 @@ __device__ __forceinline__ void block_sum_store(const double (&v)[NR], double* d
 template <class Cols>
 __device__ __forceinline__ void grid_finish(const Reducer& red, int nq, size_t stride, Cols cols) {
   __shared__ int am_last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    // thread 0 wrote all of this block's partials: publish them, then count the block
+    __threadfence();
     unsigned prev = atomicAdd(red.counter, 1u);
     am_last = (prev == gridDim.x - 1);
   }
