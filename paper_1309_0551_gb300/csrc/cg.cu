@@ -1,10 +1,11 @@
 // Conjugate gradient on M = m^2 - D_eo D_oe (even sites): plain FP64, and mixed precision
 // with FP64 reliable updates.
 //
-// One inner iteration is four kernels on the library's work stream:
+// One inner iteration is five kernels on the library's work stream:
 //   xpay    p = r + beta p                      (skipped for inactive right-hand sides)
 //   dslash  t = D_oe p                          (odd sites)
-//   dslash  Ap = m^2 p - D_eo t, pAp = <p, Ap>  (fused epilogue; last block forms alpha)
+//   dslash  Ap = m^2 p - D_eo t, <p, Ap>        (fused epilogue; per-block partials only)
+//   alpha   alpha = rr / <p,Ap>                 (one block per rhs sums the partials)
 //   update  x += alpha p, r -= alpha Ap, rr = ||r||^2 (last block forms beta, stop flag)
 // All scalars stay on the device.  `check_every` iterations are captured once as a CUDA
 // graph and replayed; between replays the host reads the per-rhs scalars (one small
@@ -57,6 +58,22 @@ template <> struct Chunk<LQ_F64> {
   __device__ __forceinline__ static void get(const vec& a, double* v) { v[0] = a.x; v[1] = a.y; }
   __device__ __forceinline__ static vec put(const double* v) { return make_double2(v[0], v[1]); }
 };
+
+// alpha = rr / <p,Ap> for each rhs (one block per rhs): <p,Ap> arrives as the per-block
+// partials of the preceding D_eo launch (FIN_DEFER, `cols` per rhs), summed here once in a
+// fixed order.  A separate one-block launch: were every block of the update kernel to sum
+// them, all of its blocks would hammer the same few L2 lines.
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, int cols, CGScalars* sc) {
+  pdl_wait();
+  const int rhs = blockIdx.x;
+  const double pAp = block_total(pap + (size_t)rhs * cols, cols);
+  if (threadIdx.x == 0) {
+    CGScalars* s = sc + rhs;
+    s->pAp = pAp;
+    s->alpha = (s->active && pAp > 0.0) ? s->rr / pAp : 0.0;
+  }
+  pdl_trigger();
+}
 
 // x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), grid-stride over
 // the rhs's 16-byte chunks.  The chunk's squares are summed in the vector precision, the
@@ -347,6 +364,7 @@ struct Solver {
   CGScalars* sc_host;    // pinned
   double* result;        // device [nrhs]
   double* partials;
+  double* dpartials;     // [nrhs][nblocks_max]: <p,Ap> partials of D_eo, summed by k_cg_alpha
   unsigned int* counter;
   int nblocks_max;
   bool pdl = false;      // programmatic dependent launch for the iteration kernels
@@ -491,7 +509,8 @@ lq_status iteration(Solver& S) {
   d.pdl = S.pdl;
   st = launch_dslash(S.ctx, d, S.s);
   if (st) return st;
-  Reducer red = S.reducer(FIN_ALPHA);
+  Reducer red = S.reducer(FIN_DEFER);
+  red.partials = S.dpartials;
   DslashArgs e = d;
   e.in = S.t;
   e.out = S.Ap;
@@ -503,6 +522,9 @@ lq_status iteration(Solver& S) {
   e.red = &red;
   st = launch_dslash(S.ctx, e, S.s);
   if (st) return st;
+  cudaError_t ce = launch_k(k_cg_alpha, dim3(S.nrhs), dim3(1024), 0, S.s, S.pdl, (const double*)S.dpartials,
+                            red.cols, S.sc);
+  if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cg_alpha");
   return launch_blas_update(S);
 }
 
@@ -825,7 +847,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = 5 * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +
-                      (size_t)nrhs * S.nblocks_max * sizeof(double) + 12 * 256;
+                      2 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
   void* base = nullptr;
   lq_status st = lq_scratch(ctx, need, &base);
   if (st) return st;
@@ -841,6 +863,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.result = (double*)A.take(sizeof(double) * nrhs);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   st = host_scalars(ctx, nrhs);
   if (st) return st;
@@ -944,7 +967,7 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +
-                      (size_t)nrhs * S.nblocks_max * sizeof(double) + 12 * 256;
+                      2 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
   if (need > kNoAllocScratchBytes)
     return lq_fail(ctx, LQ_ERR_INVALID_ARG,
                    "cg_solve_noalloc: %d right-hand sides on %d sites per parity need %zu bytes of scratch, "
@@ -964,6 +987,7 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.result = (double*)A.take(sizeof(double) * nrhs);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
   if (A.off > kNoAllocScratchBytes) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   CGScalars host_scalars[16];  // pageable host copy of the per-rhs scalars
   S.sc_host = host_scalars;

@@ -134,6 +134,7 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
     int nbx = (int)(((long long)k.G.Vh * pick.tps + pick.block - 1) / pick.block);
     if (!a.red || nbx > a.red->nblocks_max)
       return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
+    a.red->cols = nbx;  // row stride of the partials, for a FIN_DEFER consumer
   }
   cudaError_t e = fn(k, a.vec_prec, pick.block, pick.rhs_tile, pick.tps, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash");

@@ -495,6 +495,7 @@ struct Reducer {
   int nblocks_max;
   int finisher;            // what the last block does with the totals (solver specific)
   void* finisher_state;    // e.g. CG scalars
+  int cols = 0;            // host side: partial columns (row stride) of the last FIN_DEFER launch
 };
 
 lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s);

@@ -119,7 +119,10 @@ struct CGScalars {
   int pad;
 };
 
-enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+// FIN_DEFER: the blocks only store their partials; a later kernel sums them (block_total).
+// That keeps the fence, the counter atomic and the second barrier -- each an L2 round trip
+// while the block still holds its SM slot -- out of a launch with many short-lived blocks.
+enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_DEFER = 3 };
 
 __device__ __forceinline__ void finish_one(const Reducer& red, int rhs, double total) {
   CGScalars* s = reinterpret_cast<CGScalars*>(red.finisher_state) + rhs;
@@ -152,7 +155,8 @@ __device__ __forceinline__ double warp_sum(double x) {
 // Every thread of the block calls this with its NR per-rhs contributions (rhs0 + r).
 // Partials go to red.partials[rhs][bx] (bx < nbx: the block's column); the last block of
 // the grid to arrive sums them in column order (deterministic for a given launch shape)
-// and runs the finisher.  No thread ever waits on another block.
+// and runs the finisher, except under FIN_DEFER, where a later launch sums them.  No
+// thread ever waits on another block.
 template <int NR>
 __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs,
                                              int bx, int nbx) {
@@ -173,6 +177,7 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
       if (lane == 0 && rhs0 + r < nrhs) red.partials[(size_t)(rhs0 + r) * nbx + bx] = x;
     }
   }
+  if (red.finisher == FIN_DEFER) return;  // summed by the consumer after this launch
   __syncthreads();
   if (threadIdx.x == 0) {
     // thread 0 wrote this block's partials: make them visible before counting the block
@@ -199,6 +204,27 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
     }
   }
   if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// Sum of row[0, n) by the whole block in a fixed order (thread-strided sums, then a fixed
+// shuffle tree); every thread gets the total, the same in every block.  Reads through L2:
+// the row was written by an earlier launch.
+__device__ __forceinline__ double block_total(const double* row, int n) {
+  __shared__ double sm[32];
+  __shared__ double total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double x = 0.0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) x += __ldcg(row + b);
+  x = warp_sum(x);
+  if (lane == 0) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    double y = lane < nw ? sm[lane] : 0.0;
+    y = warp_sum(y);
+    if (lane == 0) total = y;
+  }
+  __syncthreads();
+  return total;
 }
 
 // The one-dimensional form: column = blockIdx.x of a (nbx, rhs tiles) grid.
