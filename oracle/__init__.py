@@ -17,8 +17,9 @@ Modules
   force      action S = Re chi^dag (m^2 - D^2) chi, dS/dchi, dS/dU and its TA projection
   improved   improved staggered Dslash (one-hop fat + three-hop Naik links), long-link builder
   md         molecular-dynamics link and momentum updates (exp, reunitarisation, leapfrog)
+  wilson     Wilson hopping term (DeGrand-Rossi gammas) and its half-spinor form (Table 1 hwvec)
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than itself
 (brute force, closed forms, invariants, finite differences); see ``tests/test_oracle_*.py``.
 """
-from . import geometry, su3, precision, dslash, cg, force, improved, md  # noqa: F401
+from . import geometry, su3, precision, dslash, cg, force, improved, md, wilson  # noqa: F401

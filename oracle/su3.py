@@ -6,8 +6,8 @@ from its Table 1 description; the adjoint mat-vec is written component by compon
 Eqs. (1.1)-(2.3) give it (first output component there; the other two are the same sum
 with the next column of A, as the text following those equations states).
 
-The two Wilson half-vector routines of Table 1 (mult_adj_su3_mat_hwvec, mult_su3_mat_hwvec)
-are not part of the staggered path and are not restated here.
+The two Wilson half-vector routines of Table 1 (mult_su3_mat_hwvec, mult_adj_su3_mat_hwvec)
+act on a half Wilson vector: two colour vectors (two spin components), array ``(..., 2, 3)``.
 """
 from __future__ import annotations
 
@@ -93,3 +93,13 @@ def scalar_mult_add_su3_matrix(A, B, s):
 def su3_projector(a, b):
     """Table 1: outer product C_ij = a_i * conj(b_j)."""
     return a[..., :, None] * np.conj(b[..., None, :])
+
+
+def mult_su3_mat_hwvec(A, h):
+    """Table 1: each of the two colour vectors of the half Wilson vector h times A."""
+    return np.stack([mult_su3_mat_vec(A, h[..., s, :]) for s in range(2)], axis=-2)
+
+
+def mult_adj_su3_mat_hwvec(A, h):
+    """Table 1: each of the two colour vectors of the half Wilson vector h times A^dag."""
+    return np.stack([mult_adj_su3_mat_vec(A, h[..., s, :]) for s in range(2)], axis=-2)

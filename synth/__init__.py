@@ -122,6 +122,19 @@ def fermion_field(dims, nrhs: int = 1, seed: int = 2, sites: str = "half") -> np
     return complex_gaussian(rng(seed), (nrhs, n, 3))
 
 
+def spinor_field(dims, nrhs: int = 1, seed: int = 2, sites: str = "half") -> np.ndarray:
+    """Gaussian Wilson spinors (4 spins x 3 colours), ``(nrhs, Vh, 4, 3)`` or ``(nrhs, V, 4, 3)``."""
+    V = volume(dims)
+    n = V // 2 if sites == "half" else V
+    return complex_gaussian(rng(seed), (nrhs, n, 4, 3))
+
+
+def hwvec_batch(n: int, seed: int = 2) -> tuple:
+    """``n`` Haar SU(3) matrices and ``n`` Gaussian half Wilson vectors (2 x 3 complex)."""
+    g = rng(seed)
+    return haar_su3(g, n), complex_gaussian(g, (n, 2, 3))
+
+
 def su3_pairs(n: int, seed: int = 2) -> tuple:
     """``n`` pairs of Haar SU(3) matrices (for the batched SU(3) products)."""
     g = rng(seed)
