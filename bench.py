@@ -356,8 +356,40 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
                                             "bytes_per_site": sb, "ring": K}
         del fats, lngs, ins, ts, outs, itmp, iout
         torch.cuda.empty_cache()
-    # multi-RHS Dslash (links loaded once per site for all right-hand sides)
+    # Wilson hopping term through half Wilson vectors (8 hops, 1320 flops per site)
     import synth
+    for prec, recon in (("f32", 18), ("f32", 12), ("bf16", 12), ("f64", 18)):
+        vec = "f64" if prec == "f64" else "f32"
+        sb = 8 * recon * BYTES[prec] + 2 * 24 * BYTES[vec]
+        K = ring_size(Vh * sb, l2, nstreams)
+        wg = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
+        dt = torch.complex128 if vec == "f64" else torch.complex64
+        host = torch.from_numpy(synth.spinor_field(DIMS, 1, seed=9)).to(dt)
+        wins = [host.cuda() for _ in range(K)]
+        wtmp = [torch.empty_like(wins[0]) for _ in range(nstreams)]
+        wout = [torch.empty_like(wins[0]) for _ in range(nstreams)]
+        vc = lq.PREC[vec]
+
+        def wstep(ss, wg=wg, wins=wins, wtmp=wtmp, wout=wout, vc=vc, K=K):
+            h = 0
+            for a in range(20):
+                s_ = ss[a % len(ss)]
+                c, c2 = h % K, (h + 1) % K
+                lq.dslash_wilson_eo(ctx, wg[c], wins[c], wtmp[a % len(ss)], 1, 1, vc, 1, s_)
+                lq.dslash_wilson_eo(ctx, wg[c2], wtmp[a % len(ss)], wout[a % len(ss)], 0, 1, vc, 1, s_)
+                h += 2
+            return 40
+        g = GraphStep(torch, wstep, nstreams)
+        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+        del g
+        us = ms * 1000.0 / launches
+        gbs = Vh * sb / us / 1e3
+        out[f"wilson/{prec}/{recon}/{vec}"] = {"gflops": round(Vh * 1320 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                               "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
+                                               "bytes_per_site": sb, "ring": K}
+        del wg, wins, wtmp, wout
+        torch.cuda.empty_cache()
+    # multi-RHS Dslash (links loaded once per site for all right-hand sides)
     for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
         sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
         K = ring_size(Vh * sb, l2, nstreams)

@@ -123,6 +123,14 @@ lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, 
 lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* c,
                            int64_t n, int adj, lq_prec prec, lq_stream stream);
 
+/* c[i] = op(A[i]) h[i] for half Wilson vectors h (two colour vectors, i.e. two spin
+ * components); op = adjoint when adj = 1.  Table 1: mult_su3_mat_hwvec (adj 0) and
+ * mult_adj_su3_mat_hwvec (adj 1).  132 flops each.
+ * A: device complex [n][3][3]; h, c: device complex [n][2][3]; prec LQ_F64 or LQ_F32;
+ * c must not overlap A or h. */
+lq_status su3_mat_hwvec_batch(lq_context* ctx, const void* A, const void* h, void* c,
+                              int64_t n, int adj, lq_prec prec, lq_stream stream);
+
 /* C[i] = A[i] + s B[i] (Table 1: scalar_mult_add_su3_matrix), e.g. the momentum update
  * P <- P + s F of a molecular-dynamics step.  A, B, C: device complex [n][3][3] of `prec`
  * (LQ_F64 or LQ_F32); C may be A or B. */
@@ -180,6 +188,22 @@ lq_status dslash_eo_improved(lq_context* ctx, const lq_gauge* fat, const lq_gaug
  * Pack L with lq_gauge_pack(..., LQ_RECON_18, ...) for dslash_eo_improved. */
 lq_status lq_long_links(lq_context* ctx, const int dims[4], const void* U_canon, double coeff,
                         void* L_canon, lq_stream stream);
+
+/* Wilson hopping term on one parity (the Wilson Dslash), the operator Table 1's half
+ * Wilson vector routines serve (the paper does not write it down):
+ *   out(x) = sum_mu [ (1 - s gamma_mu) U_mu(x) in(x+mu) + (1 + s gamma_mu) U_mu(x-mu)^dag in(x-mu) ]
+ * for x of parity `out_parity`, `in` on the other parity; s = `sign` (+1, or -1 for the
+ * adjoint: gamma_5 D gamma_5); gamma matrices in the DeGrand-Rossi (chiral) basis,
+ * gamma_5 = diag(1, 1, -1, -1); periodic; no mass or kappa factor.  Each hop projects
+ * the neighbour spinor to a half Wilson vector, multiplies it by the link
+ * (mult_su3_mat_hwvec / mult_adj_su3_mat_hwvec) and rebuilds the other two spin
+ * components: 1320 flops per output site and rhs.
+ *   U: any packed gauge (the staggered phases are not in the links).
+ *   in, out: device spinor fields [nrhs][Vh][4][3] complex, [spin][colour]; LQ_F64 for
+ *   LQ_F64 links, LQ_F32 for LQ_F32 / LQ_BF16 / LQ_F16 links (FP32 arithmetic); must not
+ *   overlap.  nrhs in [1, 16]. */
+lq_status dslash_wilson_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
+                           int out_parity, int nrhs, lq_prec vec_prec, int sign, lq_stream stream);
 
 /* ---------------------------------------------------------------------- CG ---------- */
 

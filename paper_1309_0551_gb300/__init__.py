@@ -82,6 +82,8 @@ def load(path: str | None = None):
         "lq_long_links": ([P, ctypes.POINTER(I), P, D, P, P], I),
         "su3_scalar_mult_add_batch": ([P, P, P, P, D, L, I, P], I),
         "su3_exp_mul_batch": ([P, P, P, P, D, L, I, P], I),
+        "su3_mat_hwvec_batch": ([P, P, P, P, L, I, I, P], I),
+        "dslash_wilson_eo": ([P, P, P, P, I, I, I, I, P], I),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -204,6 +206,15 @@ def dslash_eo_improved(ctx: Context, fat: Gauge, lng: Gauge, inp, out, out_parit
                                          int(out_parity), int(nrhs), int(vp), _stream(stream)))
 
 
+def dslash_wilson_eo(ctx: Context, U: Gauge, inp, out, out_parity: int, nrhs: int = 1, vec_prec=None,
+                     sign: int = 1, stream=None):
+    """Wilson hopping term on parity ``out_parity`` (canonical [nrhs][Vh][4][3] spinors);
+    ``sign`` -1 applies the adjoint."""
+    vp = vec_prec_of(inp) if vec_prec is None else vec_prec
+    ctx.check(ctx.lib.dslash_wilson_eo(ctx.handle, U.handle, _ptr(inp), _ptr(out), int(out_parity),
+                                       int(nrhs), int(vp), int(sign), _stream(stream)))
+
+
 def lq_long_links(ctx: Context, dims, U, coeff: float, L, stream=None):
     """L_mu(x) = coeff * U_mu(x) U_mu(x+mu) U_mu(x+2mu) (canonical complex128 tensors)."""
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
@@ -252,6 +263,15 @@ def su3_matvec_batch(ctx: Context, A, b, c, n=None, adj=0, prec=None, stream=Non
     prec = vec_prec_of(A) if prec is None else prec
     ctx.check(ctx.lib.su3_matvec_batch(ctx.handle, _ptr(A), _ptr(b), _ptr(c), int(n), int(adj),
                                        int(prec), _stream(stream)))
+
+
+def su3_mat_hwvec_batch(ctx: Context, A, h, c, n=None, adj=0, prec=None, stream=None):
+    """c[i] = op(A[i]) h[i] for half Wilson vectors (Table 1: mult_su3_mat_hwvec /
+    mult_adj_su3_mat_hwvec)."""
+    n = A.shape[0] if n is None else n
+    prec = vec_prec_of(A) if prec is None else prec
+    ctx.check(ctx.lib.su3_mat_hwvec_batch(ctx.handle, _ptr(A), _ptr(h), _ptr(c), int(n), int(adj),
+                                          int(prec), _stream(stream)))
 
 
 def _cg_call(fn, ctx, U_hi, U_lo, mass, b, x, nrhs, tol, maxiter, reliable_every, delta,

@@ -1,5 +1,6 @@
 // Batched SU(3) products of Table 1: mult_su3_nn / mult_su3_an / mult_su3_na
-// (su3_mul_batch) and mult_su3_mat_vec / mult_adj_su3_mat_vec (su3_matvec_batch).
+// (su3_mul_batch), mult_su3_mat_vec / mult_adj_su3_mat_vec (su3_matvec_batch) and the two
+// half Wilson vector routines (su3_mat_hwvec_batch).
 //
 // The operands arrive in the canonical array-of-structures layout (one 3x3 complex matrix
 // = 18 contiguous reals).  A block's slice of every operand is one contiguous range: it is
@@ -152,6 +153,34 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
   stage_out(c + base * 6, sb, cnt * 6);
 }
 
+// c = op(A) h for a half Wilson vector h (two colour vectors, 12 reals):
+// mult_su3_mat_hwvec (ADJ 0) and mult_adj_su3_mat_hwvec (ADJ 1) of Table 1.
+template <class T, int ADJ>
+__global__ void __launch_bounds__(kThreads) k_su3_hwvec(const T* __restrict__ A, const T* __restrict__ h,
+                                                        T* __restrict__ c, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  T* sA = reinterpret_cast<T*>(smem_raw);
+  T* sh = sA + kThreads * 18;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  if (!stage_in(sA, A + base * 18, cnt * 18, sh, h + base * 12, cnt * 12, &bar)) return;
+  if ((int)threadIdx.x < cnt) {
+    T a[18], v[12], r[12];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) a[k] = sA[threadIdx.x * 18 + k];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { v[k] = sh[threadIdx.x * 12 + k]; r[k] = 0; }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      if (ADJ) adj_mat_vec_acc(a, v + 6 * sp, r + 6 * sp, T(1));
+      else mat_vec_acc(a, v + 6 * sp, r + 6 * sp, T(1));
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sh[threadIdx.x * 12 + k] = r[k];
+  }
+  stage_out(c + base * 12, sh, cnt * 12);
+}
 
 // C = A + s B (scalar_mult_add_su3_matrix, Table 1); C may be A or B (same element).
 template <class T>
@@ -292,6 +321,15 @@ cudaError_t launch_matvec(const void* A, const void* b, void* c, int64_t n, int 
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_hwvec(const void* A, const void* h, void* c, int64_t n, int adj, cudaStream_t s) {
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  const size_t smem = kThreads * 30 * sizeof(T);
+  if (adj) k_su3_hwvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n);
+  else k_su3_hwvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -334,6 +372,25 @@ extern "C" lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = prec == LQ_F64 ? launch_matvec<double>(A, b, c, n, adj, s) : launch_matvec<float>(A, b, c, n, adj, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_matvec");
+  return LQ_OK;
+}
+
+extern "C" lq_status su3_mat_hwvec_batch(lq_context* ctx, const void* A, const void* h, void* c, int64_t n,
+                                         int adj, lq_prec prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (prec != LQ_F64 && prec != LQ_F32) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "su3_mat_hwvec_batch supports LQ_F64 and LQ_F32");
+  if (adj != 0 && adj != 1) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "adj must be 0 or 1");
+  if (n == 0) return LQ_OK;
+  if (!A || !h || !c) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL operand");
+  if (!lq_aligned16(A) || !lq_aligned16(h) || !lq_aligned16(c)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be 16-byte aligned");
+  const size_t es = lq_prec_bytes(prec);
+  if (overlaps(c, (size_t)n * 12 * es, A, (size_t)n * 18 * es) || overlaps(c, (size_t)n * 12 * es, h, (size_t)n * 12 * es))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "c overlaps A or h");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = prec == LQ_F64 ? launch_hwvec<double>(A, h, c, n, adj, s) : launch_hwvec<float>(A, h, c, n, adj, s);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_hwvec");
   return LQ_OK;
 }
 

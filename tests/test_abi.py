@@ -48,3 +48,5 @@ def test_status_strings_and_null_context(lib):
     assert lib.dslash_eo(None, None, None, None, 0, 1, 0, None) == 1
     assert lib.su3_mul_batch(None, None, None, None, ctypes.c_int64(1), 0, 0, 0, None) == 1
     assert lib.cg_solve(None, None, None, ctypes.c_double(0.1), None, None, 1, None, None, None) == 1
+    assert lib.dslash_wilson_eo(None, None, None, None, 0, 1, 0, 1, None) == 1
+    assert lib.su3_mat_hwvec_batch(None, None, None, None, ctypes.c_int64(1), 0, 0, None) == 1
