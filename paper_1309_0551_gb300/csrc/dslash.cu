@@ -106,12 +106,21 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   }
   TuneEntry pick;
   const TuneEntry& f = ctx->forced;
+  // the rhs-per-warp kernel: FP32 vectors, no fused reduction, two or more rhs
+  const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.reduce == RED_NONE && a.nrhs >= 2;
   if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
-      !(a.U->prec == LQ_F64 && f.rhs_tile > 4)) {
+      !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && f.block == 32 * f.rhs_tile))) {
     pick = f;
   } else {
     std::string key = dslash_key(a.U, a.vec_prec, a.nrhs);
     std::vector<TuneEntry> cands = dslash_candidates(a.U->prec, a.nrhs);
+    if (rw_ok)
+      for (int t : {2, 4, 8})
+        if (t <= a.nrhs) {
+          TuneEntry e;
+          e.block = 32 * t; e.rhs_tile = t; e.tps = kTpsRhsWarps;
+          cands.push_back(e);
+        }
     if (a.reduce != RED_NONE) {
       key += a.reduce == RED_DOT ? " red=dot" : " red=norm";
       std::vector<TuneEntry> fit;  // every candidate must fit the reduction scratch

@@ -65,9 +65,96 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 
+// Multi-RHS half Dslash with one thread per (output site, rhs): a block holds 32 sites
+// (lanes) x RT right-hand sides (warps).  Warp w loads the links of hop w (and w + RT, ...)
+// for the block's 32 sites once, rebuilds them, folds in the hop's sign and writes op(U)
+// (U_mu(x) forward, U_mu(x-mu)^dag backward) to shared memory with the neighbour index;
+// after one barrier every thread issues its eight neighbour-vector loads at once and
+// applies the eight shared links.  Link loads and the 12-real reconstruction are done
+// once per site and hop, not once per rhs, and no thread holds more than one rhs.
+// FP32 vectors and arithmetic; no fused reduction (RED_NONE).
+template <lq_prec GP, int R, int RT>
+__global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
+  using L = LinkT<GP, R>;
+  using VT = VecT<LQ_F32>;
+  __shared__ float2 sU[8][9][32];   // [hop][element 3i+j of op(U), sign folded][site]
+  __shared__ int sN[8][32];         // [hop][site]: checkerboard index of the neighbour
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const Geom& G = a.G;
+  const int cb = blockIdx.x * 32 + lane;
+  const int cbc = cb < G.Vh ? cb : G.Vh - 1;   // lanes past the end work on a valid site
+  const int xh = cbc % G.Lxh;
+  const int row = cbc / G.Lxh;
+  const int y = row % G.Ly;
+  const int zt = row / G.Ly;
+  const int z = zt % G.Lz;
+  const int t = zt / G.Lz;
+  const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+  pdl_wait();
+  for (int h = w; h < 8; h += RT) {
+    const int mu = h >> 1;
+    const bool bwd = h & 1;
+    int cbf, cbb;
+    dslash_neighbours(G, mu, x, y, z, t, xh, row, cbf, cbb);
+    const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+    const float sg = ((ephase & 1) ? -1.f : 1.f) * (bwd ? -1.f : 1.f);
+    float u[18];
+    L::load(a.gauge + (size_t)(2 * mu + (bwd ? 1 - a.out_par : a.out_par)) * a.blk_bytes, G.S, bwd ? cbb : cbc, u);
+    if (R == 12) reconstruct_row2(u);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float er = bwd ? u[6 * j + 2 * i] : u[6 * i + 2 * j];
+        const float ei = bwd ? -u[6 * j + 2 * i + 1] : u[6 * i + 2 * j + 1];
+        sU[h][3 * i + j][lane] = make_float2(sg * er, sg * ei);
+      }
+    sN[h][lane] = bwd ? cbb : cbf;
+  }
+  __syncthreads();
+  const int rhs = blockIdx.y * RT + w;
+  if (rhs >= a.nrhs) return;
+  const size_t rbase = (size_t)rhs * a.rhs_stride;
+  float v[8][6];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) VT::load(a.in, rbase + sN[h][lane], v[h]);
+  float acc[1][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int h = 0; h < 8; ++h)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float2 e = sU[h][3 * i + j][lane];
+        acc[0][2 * i] = fmaf(e.x, v[h][2 * j], acc[0][2 * i]);
+        acc[0][2 * i] = fmaf(-e.y, v[h][2 * j + 1], acc[0][2 * i]);
+        acc[0][2 * i + 1] = fmaf(e.x, v[h][2 * j + 1], acc[0][2 * i + 1]);
+        acc[0][2 * i + 1] = fmaf(e.y, v[h][2 * j], acc[0][2 * i + 1]);
+      }
+  pdl_trigger();
+  if (cb < G.Vh) {
+    double part[1] = {0.0};
+    dslash_epilogue<LQ_F32, 1, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED_NONE, a.rhs_stride, a.nrhs, rhs,
+                                  cb, 0, part);
+  }
+}
+
+template <lq_prec GP, int R>
+static cudaError_t launch_dslash_rw(const DslashKArgs& k, int tile, cudaStream_t s) {
+  dim3 grid((unsigned)((k.G.Vh + 31) / 32), (unsigned)((k.nrhs + tile - 1) / tile));
+  switch (tile) {
+    case 2: return launch_k(k_dslash_rw<GP, R, 2>, grid, dim3(32, 2), 0, s, k.pdl != 0, k);
+    case 4: return launch_k(k_dslash_rw<GP, R, 4>, grid, dim3(32, 4), 0, s, k.pdl != 0, k);
+    case 8: return launch_k(k_dslash_rw<GP, R, 8>, grid, dim3(32, 8), 0, s, k.pdl != 0, k);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Host side: launch one instance.  Supported (rhs tile, threads per site) pairs:
-// (1|2, 1|2|4), (4, 1|2), (8, 1); dslash_shape_ok() tells the tuner.
+// (1|2, 1|2|4), (4, 1|2), (8, 1), and (2|4|8, kTpsRhsWarps) for k_dslash_rw;
+// dslash_shape_ok() tells the tuner.
 inline bool dslash_shape_ok(int tile, int tps) {
+  if (tps == kTpsRhsWarps) return tile == 2 || tile == 4 || tile == 8;
   if (tile == 1 || tile == 2) return tps == 1 || tps == 2 || tps == 4;
   if (tile == 4) return tps == 1 || tps == 2;
   return tile == 8 && tps == 1;
@@ -82,6 +169,14 @@ static cudaError_t launch_dslash_inst(const DslashKArgs& k, int block, cudaStrea
 
 template <lq_prec GP, int R, lq_prec VP>
 static cudaError_t launch_dslash_shape(const DslashKArgs& k, int block, int tile, int tps, cudaStream_t s) {
+  if (tps == kTpsRhsWarps) {
+    if constexpr (GP != LQ_F64 && VP == LQ_F32) {
+      if (k.reduce != RED_NONE || block != 32 * tile) return cudaErrorInvalidValue;
+      return launch_dslash_rw<GP, R>(k, tile, s);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   switch (tile * 8 + tps) {
     case 1 * 8 + 1: return launch_dslash_inst<GP, R, VP, 1, 1>(k, block, s);
     case 1 * 8 + 2: return launch_dslash_inst<GP, R, VP, 1, 2>(k, block, s);

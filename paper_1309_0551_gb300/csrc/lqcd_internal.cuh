@@ -19,8 +19,12 @@ struct TuneEntry {
   int block = 0;      // threads per block
   int rhs_tile = 1;   // right-hand sides per thread (Dslash)
   float us = 0.f;     // best measured time
-  int tps = 1;        // threads per output site (Dslash)
+  int tps = 1;        // threads per output site (Dslash); kTpsRhsWarps: the rhs-per-warp kernel
 };
+
+// TuneEntry::tps value that selects the multi-RHS Dslash with one thread per (site, rhs):
+// blocks of 32 sites x rhs_tile warps, links shared through shared memory (k_dslash_rw).
+constexpr int kTpsRhsWarps = 8;
 
 struct lq_context {
   int device = 0;

@@ -86,13 +86,15 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
   // default mode, within 15% in the throughput mode (several independent launches in
   // flight fill the GPU, so a launch's own parallelism matters less than its instruction
   // count) -- take the one doing the least redundant work: fewest threads per site, most
-  // right-hand sides per thread, then the candidate order.
+  // right-hand sides sharing each loaded link (per thread, or per block for the
+  // rhs-per-warp kernel, which runs one thread per site and rhs), then the candidate order.
   const float tol = ctx->tune_mode == 2 ? 1.15f : 1.03f;
+  auto tps_of = [](const TuneEntry& t) { return t.tps == kTpsRhsWarps ? 1 : t.tps; };
   TuneEntry best;
   bool have = false;
   for (const TuneEntry& t : timed) {
     if (t.us > tol * best_us) continue;
-    if (!have || t.tps < best.tps || (t.tps == best.tps && t.rhs_tile > best.rhs_tile)) {
+    if (!have || tps_of(t) < tps_of(best) || (tps_of(t) == tps_of(best) && t.rhs_tile > best.rhs_tile)) {
       best = t;
       have = true;
     }

@@ -123,3 +123,31 @@ def test_dslash_multi_matches_single(lq, ctx, gp, recon, vp, nrhs):
     torch.cuda.synchronize()
     for o, r in zip(outs, refs):
         assert rel_l2(from_device_vec(o), r) < store_tolerance(vp)
+
+
+@pytest.mark.parametrize("gp,recon", [("f32", 12), ("f32", 18), ("bf16", 12), ("f16", 18)])
+@pytest.mark.parametrize("tile", [2, 4, 8])
+@pytest.mark.parametrize("nrhs", [3, 8, 13])
+def test_rhs_warp_kernel(lq, gp, recon, tile, nrhs, monkeypatch):
+    """The one-thread-per-(site, rhs) multi-RHS kernel (shape block = 32 x tile, tps 8),
+    forced through the shape override, on a lattice whose half volume (240) is not a
+    multiple of 32 and rhs counts that leave a partial tile."""
+    import torch
+    monkeypatch.setenv("LQCD_DSLASH_SHAPE", f"{32 * tile},{tile},8")
+    ctx = lq.Context(0)
+    dims = (6, 4, 2, 10)
+    U = synth.gauge_field(dims, "haar", seed=66)
+    g = lq.lq_gauge_pack(ctx, dims, torch.from_numpy(U).cuda(), gp, recon)
+    Uq = quantize_links(U, gp, recon)
+    for parity in (0, 1):
+        chi = synth.fermion_field(dims, nrhs, seed=67 + parity)
+        d = to_device_vec(chi, "f32")
+        out = empty_vec(chi.shape, "f32")
+        lq.dslash_eo(ctx, g, d, out, parity, nrhs)
+        torch.cuda.synchronize()
+        ref = odslash.dslash_eo_multi(Uq, from_device_vec(d), dims, parity)
+        got = from_device_vec(out)
+        for k in range(nrhs):
+            assert rel_l2(got[k], ref[k]) < store_tolerance("f32")
+    if tile <= nrhs:
+        assert ctx.tune_report() == ""      # the forced shape was taken: nothing was tuned
