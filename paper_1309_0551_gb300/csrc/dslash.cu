@@ -109,16 +109,18 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   // the rhs-per-warp kernel: FP32 vectors, no fused reduction, two or more rhs
   const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.reduce == RED_NONE && a.nrhs >= 2;
   if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
-      !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && f.block == 32 * f.rhs_tile))) {
+      !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && dslash_rw_shape_ok(f.block, f.rhs_tile)))) {
     pick = f;
   } else {
     std::string key = dslash_key(a.U, a.vec_prec, a.nrhs);
     std::vector<TuneEntry> cands = dslash_candidates(a.U->prec, a.nrhs);
     if (rw_ok)
-      for (int t : {2, 4, 8})
-        if (t <= a.nrhs) {
+      for (int rt : {2, 4, 8})
+        for (int nrt : {1, 2, 4}) {
+          const int t = rt * nrt;
+          if (t > a.nrhs || !dslash_rw_shape_ok(32 * rt, t)) continue;
           TuneEntry e;
-          e.block = 32 * t; e.rhs_tile = t; e.tps = kTpsRhsWarps;
+          e.block = 32 * rt; e.rhs_tile = t; e.tps = kTpsRhsWarps;
           cands.push_back(e);
         }
     if (a.reduce != RED_NONE) {

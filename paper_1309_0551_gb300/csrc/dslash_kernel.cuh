@@ -65,15 +65,16 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 
-// Multi-RHS half Dslash with one thread per (output site, rhs): a block holds 32 sites
-// (lanes) x RT right-hand sides (warps).  Warp w loads the links of hop w (and w + RT, ...)
-// for the block's 32 sites once, rebuilds them, folds in the hop's sign and writes op(U)
-// (U_mu(x) forward, U_mu(x-mu)^dag backward) to shared memory with the neighbour index;
-// after one barrier every thread issues its eight neighbour-vector loads at once and
-// applies the eight shared links.  Link loads and the 12-real reconstruction are done
-// once per site and hop, not once per rhs, and no thread holds more than one rhs.
+// Multi-RHS half Dslash with the right-hand sides spread over warps: a block holds 32
+// sites (lanes) x RT warps, each thread NRT right-hand sides of one site.  Warp w loads the
+// links of hop w (and w + RT, ...) for the block's 32 sites once, rebuilds them, folds in
+// the hop's sign and writes op(U) (U_mu(x) forward, U_mu(x-mu)^dag backward) to shared
+// memory with the neighbour index; after one barrier every thread applies the eight shared
+// links to its right-hand sides.  Link loads and the 12-real reconstruction are done once
+// per site and hop, not once per rhs; each link element read from shared memory serves
+// NRT right-hand sides (in pairs, with packed FP32x2 FMAs, when NRT is even).
 // FP32 vectors and arithmetic; no fused reduction (RED_NONE).
-template <lq_prec GP, int R, int RT>
+template <lq_prec GP, int R, int RT, int NRT>
 __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
   using L = LinkT<GP, R>;
   using VT = VecT<LQ_F32>;
@@ -112,49 +113,118 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
     sN[h][lane] = bwd ? cbb : cbf;
   }
   __syncthreads();
-  const int rhs = blockIdx.y * RT + w;
-  if (rhs >= a.nrhs) return;
-  const size_t rbase = (size_t)rhs * a.rhs_stride;
-  float v[8][6];
+  const int rhs0 = (blockIdx.y * RT + w) * NRT;
+  if (rhs0 >= a.nrhs) return;
+  float acc[NRT][6];
+  if constexpr (NRT == 1) {
+    // all eight neighbour loads in flight at once
+    const size_t rbase = (size_t)rhs0 * a.rhs_stride;
+    float v[8][6];
 #pragma unroll
-  for (int h = 0; h < 8; ++h) VT::load(a.in, rbase + sN[h][lane], v[h]);
-  float acc[1][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+    for (int h = 0; h < 8; ++h) VT::load(a.in, rbase + sN[h][lane], v[h]);
 #pragma unroll
-  for (int h = 0; h < 8; ++h)
+    for (int k = 0; k < 6; ++k) acc[0][k] = 0.f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int h = 0; h < 8; ++h)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float2 e = sU[h][3 * i + j][lane];
-        acc[0][2 * i] = fmaf(e.x, v[h][2 * j], acc[0][2 * i]);
-        acc[0][2 * i] = fmaf(-e.y, v[h][2 * j + 1], acc[0][2 * i]);
-        acc[0][2 * i + 1] = fmaf(e.x, v[h][2 * j + 1], acc[0][2 * i + 1]);
-        acc[0][2 * i + 1] = fmaf(e.y, v[h][2 * j], acc[0][2 * i + 1]);
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float2 e = sU[h][3 * i + j][lane];
+          acc[0][2 * i] = fmaf(e.x, v[h][2 * j], acc[0][2 * i]);
+          acc[0][2 * i] = fmaf(-e.y, v[h][2 * j + 1], acc[0][2 * i]);
+          acc[0][2 * i + 1] = fmaf(e.x, v[h][2 * j + 1], acc[0][2 * i + 1]);
+          acc[0][2 * i + 1] = fmaf(e.y, v[h][2 * j], acc[0][2 * i + 1]);
+        }
+  } else {
+    static_assert(NRT % 2 == 0, "NRT must be 1 or even");
+    // right-hand sides in pairs (lane x: rhs0 + 2p, lane y: rhs0 + 2p + 1); the next hop's
+    // vectors are loaded before this hop's arithmetic.  A partial tile repeats the last
+    // right-hand side in its loads; the epilogue stores only the valid ones.
+    size_t roff[NRT];
+#pragma unroll
+    for (int r = 0; r < NRT; ++r) roff[r] = (size_t)min(rhs0 + r, a.nrhs - 1) * a.rhs_stride;
+    float2 acc2[NRT / 2][6];
+#pragma unroll
+    for (int p = 0; p < NRT / 2; ++p)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc2[p][k] = make_float2(0.f, 0.f);
+    float v[2][NRT][6];
+#pragma unroll
+    for (int r = 0; r < NRT; ++r) VT::load(a.in, roff[r] + sN[0][lane], v[0][r]);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const int cur = h & 1;
+      if (h + 1 < 8) {
+#pragma unroll
+        for (int r = 0; r < NRT; ++r) VT::load(a.in, roff[r] + sN[h + 1][lane], v[cur ^ 1][r]);
       }
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const float2 e = sU[h][3 * i + j][lane];
+          const float2 E = make_float2(e.x, e.x), F = make_float2(e.y, e.y), N = make_float2(-e.y, -e.y);
+#pragma unroll
+          for (int p = 0; p < NRT / 2; ++p) {
+            const float2 vr = make_float2(v[cur][2 * p][2 * j], v[cur][2 * p + 1][2 * j]);
+            const float2 vi = make_float2(v[cur][2 * p][2 * j + 1], v[cur][2 * p + 1][2 * j + 1]);
+            acc2[p][2 * i] = __ffma2_rn(E, vr, acc2[p][2 * i]);
+            acc2[p][2 * i] = __ffma2_rn(N, vi, acc2[p][2 * i]);
+            acc2[p][2 * i + 1] = __ffma2_rn(E, vi, acc2[p][2 * i + 1]);
+            acc2[p][2 * i + 1] = __ffma2_rn(F, vr, acc2[p][2 * i + 1]);
+          }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NRT / 2; ++p)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[2 * p][k] = acc2[p][k].x;
+        acc[2 * p + 1][k] = acc2[p][k].y;
+      }
+  }
   pdl_trigger();
   if (cb < G.Vh) {
-    double part[1] = {0.0};
-    dslash_epilogue<LQ_F32, 1, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED_NONE, a.rhs_stride, a.nrhs, rhs,
-                                  cb, 0, part);
+    double part[NRT];
+#pragma unroll
+    for (int r = 0; r < NRT; ++r) part[r] = 0.0;
+    dslash_epilogue<LQ_F32, NRT, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED_NONE, a.rhs_stride, a.nrhs, rhs0,
+                                    cb, 0, part);
   }
 }
 
+// Shapes of k_dslash_rw: block = 32 x RT threads, rhs_tile = RT x NRT right-hand sides.
+inline bool dslash_rw_shape_ok(int block, int tile) {
+  if (block % 32 || tile % (block / 32)) return false;
+  const int rt = block / 32, nrt = tile / rt;
+  return (rt == 2 || rt == 4 || rt == 8) && (nrt == 1 || nrt == 2 || nrt == 4) && rt * nrt <= 16;
+}
+
 template <lq_prec GP, int R>
-static cudaError_t launch_dslash_rw(const DslashKArgs& k, int tile, cudaStream_t s) {
+static cudaError_t launch_dslash_rw(const DslashKArgs& k, int block, int tile, cudaStream_t s) {
+  if (!dslash_rw_shape_ok(block, tile)) return cudaErrorInvalidValue;
+  const int rt = block / 32, nrt = tile / rt;
   dim3 grid((unsigned)((k.G.Vh + 31) / 32), (unsigned)((k.nrhs + tile - 1) / tile));
-  switch (tile) {
-    case 2: return launch_k(k_dslash_rw<GP, R, 2>, grid, dim3(32, 2), 0, s, k.pdl != 0, k);
-    case 4: return launch_k(k_dslash_rw<GP, R, 4>, grid, dim3(32, 4), 0, s, k.pdl != 0, k);
-    case 8: return launch_k(k_dslash_rw<GP, R, 8>, grid, dim3(32, 8), 0, s, k.pdl != 0, k);
+  const bool pdl = k.pdl != 0;
+  switch (rt * 8 + nrt) {
+    case 2 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 2, 1>, grid, dim3(32, 2), 0, s, pdl, k);
+    case 2 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 2, 2>, grid, dim3(32, 2), 0, s, pdl, k);
+    case 2 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 2, 4>, grid, dim3(32, 2), 0, s, pdl, k);
+    case 4 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 4, 1>, grid, dim3(32, 4), 0, s, pdl, k);
+    case 4 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 4, 2>, grid, dim3(32, 4), 0, s, pdl, k);
+    case 4 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 4, 4>, grid, dim3(32, 4), 0, s, pdl, k);
+    case 8 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 8, 1>, grid, dim3(32, 8), 0, s, pdl, k);
+    case 8 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 8, 2>, grid, dim3(32, 8), 0, s, pdl, k);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // Host side: launch one instance.  Supported (rhs tile, threads per site) pairs:
-// (1|2, 1|2|4), (4, 1|2), (8, 1), and (2|4|8, kTpsRhsWarps) for k_dslash_rw;
-// dslash_shape_ok() tells the tuner.
+// (1|2, 1|2|4), (4, 1|2), (8, 1), and (RT x NRT, kTpsRhsWarps) for k_dslash_rw;
+// dslash_shape_ok() (and dslash_rw_shape_ok()) tell the tuner.
 inline bool dslash_shape_ok(int tile, int tps) {
-  if (tps == kTpsRhsWarps) return tile == 2 || tile == 4 || tile == 8;
+  if (tps == kTpsRhsWarps) return tile >= 2 && tile <= 16;   // with the block: dslash_rw_shape_ok
   if (tile == 1 || tile == 2) return tps == 1 || tps == 2 || tps == 4;
   if (tile == 4) return tps == 1 || tps == 2;
   return tile == 8 && tps == 1;
@@ -171,8 +241,8 @@ template <lq_prec GP, int R, lq_prec VP>
 static cudaError_t launch_dslash_shape(const DslashKArgs& k, int block, int tile, int tps, cudaStream_t s) {
   if (tps == kTpsRhsWarps) {
     if constexpr (GP != LQ_F64 && VP == LQ_F32) {
-      if (k.reduce != RED_NONE || block != 32 * tile) return cudaErrorInvalidValue;
-      return launch_dslash_rw<GP, R>(k, tile, s);
+      if (k.reduce != RED_NONE) return cudaErrorInvalidValue;
+      return launch_dslash_rw<GP, R>(k, block, tile, s);
     } else {
       return cudaErrorInvalidValue;
     }

@@ -126,14 +126,16 @@ def test_dslash_multi_matches_single(lq, ctx, gp, recon, vp, nrhs):
 
 
 @pytest.mark.parametrize("gp,recon", [("f32", 12), ("f32", 18), ("bf16", 12), ("f16", 18)])
-@pytest.mark.parametrize("tile", [2, 4, 8])
+@pytest.mark.parametrize("block,tile", [(64, 2), (128, 4), (256, 8), (256, 16), (128, 8), (64, 4), (64, 8),
+                                        (128, 16)])
 @pytest.mark.parametrize("nrhs", [3, 8, 13])
-def test_rhs_warp_kernel(lq, gp, recon, tile, nrhs, monkeypatch):
-    """The one-thread-per-(site, rhs) multi-RHS kernel (shape block = 32 x tile, tps 8),
-    forced through the shape override, on a lattice whose half volume (240) is not a
-    multiple of 32 and rhs counts that leave a partial tile."""
+def test_rhs_warp_kernel(lq, gp, recon, block, tile, nrhs, monkeypatch):
+    """The multi-RHS kernel with the right-hand sides spread over warps (block = 32 sites x
+    block/32 warps, tile/(block/32) rhs per thread, tps 8), forced through the shape
+    override, on a lattice whose half volume (240) is not a multiple of 32 and rhs counts
+    that leave a partial tile."""
     import torch
-    monkeypatch.setenv("LQCD_DSLASH_SHAPE", f"{32 * tile},{tile},8")
+    monkeypatch.setenv("LQCD_DSLASH_SHAPE", f"{block},{tile},8")
     ctx = lq.Context(0)
     dims = (6, 4, 2, 10)
     U = synth.gauge_field(dims, "haar", seed=66)
