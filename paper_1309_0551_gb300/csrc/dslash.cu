@@ -224,19 +224,48 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
                               const std::string& key, cudaStream_t s) {
   MultiLaunchFn fn = dslash_multi_fn(gp, recon);
   if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
+  // Tuning launches must be repeatable: the plain operator, or a launch with a reduction
+  // tuned as itself (its cost depends on the shape; the solvers never let out alias w1 or
+  // w2, and their finishers only store totals or alpha = rr / total).
   MultiKArgs plain = a;
-  for (int l = 0; l < a.nlat; ++l) plain.lat[l].w1 = plain.lat[l].w2 = nullptr;
-  plain.c = 1.0;
-  plain.reduce = RED_NONE;
-  plain.skip_state = nullptr;
+  if (a.reduce == RED_NONE) {
+    for (int l = 0; l < a.nlat; ++l) plain.lat[l].w1 = plain.lat[l].w2 = nullptr;
+    plain.c = 1.0;
+    plain.skip_state = nullptr;
+  }
+  const bool rw_ok = gp != LQ_F64 && vp == LQ_F32 && a.nrhs >= 2;
   TuneEntry pick;
   const TuneEntry& f = ctx->forced;
   if (f.block && dslash_multi_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
-      !(gp == LQ_F64 && f.rhs_tile > 4)) {
+      !(gp == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && dslash_rw_shape_ok(f.block, f.rhs_tile)))) {
     pick = f;
   } else {
+    std::vector<TuneEntry> cands = multi_candidates(gp, a.nrhs);
+    if (rw_ok)
+      for (int rt : {2, 4, 8})
+        for (int nrt : {1, 2, 4}) {
+          const int t = rt * nrt;
+          if (t > a.nrhs || !dslash_rw_shape_ok(32 * rt, t)) continue;
+          TuneEntry e;
+          e.block = 32 * rt; e.rhs_tile = t; e.tps = kTpsRhsWarps;
+          cands.push_back(e);
+        }
+    std::string tkey = key;
+    if (a.reduce != RED_NONE) {
+      tkey += a.reduce == RED_DOT ? " red=dot" : " red=norm";
+      std::vector<TuneEntry> fit;   // every candidate must fit the reduction scratch
+      for (const TuneEntry& c : cands) {
+        MultiKArgs chk = a;
+        multi_tiles(chk, c.block, c.rhs_tile, c.tps);
+        bool ok = true;
+        for (int l = 0; l < a.nlat; ++l) ok &= (size_t)chk.lat[l].tiles_x <= a.pstride;
+        if (ok) fit.push_back(c);
+      }
+      if (fit.empty()) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
+      cands = fit;
+    }
     lq_status st = tune_pick(
-        ctx, key, multi_candidates(gp, a.nrhs), s,
+        ctx, tkey, cands, s,
         [&](const TuneEntry& c) -> lq_status {
           cudaError_t e = fn(plain, vp, c.block, c.rhs_tile, c.tps, ctx->num_sms, s);
           if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi (tuning)");

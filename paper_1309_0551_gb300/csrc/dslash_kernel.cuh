@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
   using VT = VecT<LQ_F32>;
   __shared__ float2 sU[8][9][32];   // [hop][element 3i+j of op(U), sign folded][site]
   __shared__ int sN[8][32];         // [hop][site]: checkerboard index of the neighbour
-  const int lane = threadIdx.x, w = threadIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 1-D block of 32 x RT threads
   const Geom& G = a.G;
   const int cb = blockIdx.x * 32 + lane;
   const int cbc = cb < G.Vh ? cb : G.Vh - 1;   // lanes past the end work on a valid site
@@ -208,14 +208,14 @@ static cudaError_t launch_dslash_rw(const DslashKArgs& k, int block, int tile, c
   dim3 grid((unsigned)((k.G.Vh + 31) / 32), (unsigned)((k.nrhs + tile - 1) / tile));
   const bool pdl = k.pdl != 0;
   switch (rt * 8 + nrt) {
-    case 2 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 2, 1>, grid, dim3(32, 2), 0, s, pdl, k);
-    case 2 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 2, 2>, grid, dim3(32, 2), 0, s, pdl, k);
-    case 2 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 2, 4>, grid, dim3(32, 2), 0, s, pdl, k);
-    case 4 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 4, 1>, grid, dim3(32, 4), 0, s, pdl, k);
-    case 4 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 4, 2>, grid, dim3(32, 4), 0, s, pdl, k);
-    case 4 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 4, 4>, grid, dim3(32, 4), 0, s, pdl, k);
-    case 8 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 8, 1>, grid, dim3(32, 8), 0, s, pdl, k);
-    case 8 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 8, 2>, grid, dim3(32, 8), 0, s, pdl, k);
+    case 2 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 2, 1>, grid, dim3(64), 0, s, pdl, k);
+    case 2 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 2, 2>, grid, dim3(64), 0, s, pdl, k);
+    case 2 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 2, 4>, grid, dim3(64), 0, s, pdl, k);
+    case 4 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 4, 1>, grid, dim3(128), 0, s, pdl, k);
+    case 4 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 4, 2>, grid, dim3(128), 0, s, pdl, k);
+    case 4 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 4, 4>, grid, dim3(128), 0, s, pdl, k);
+    case 8 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 8, 1>, grid, dim3(256), 0, s, pdl, k);
+    case 8 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 8, 2>, grid, dim3(256), 0, s, pdl, k);
     default: return cudaErrorInvalidValue;
   }
 }

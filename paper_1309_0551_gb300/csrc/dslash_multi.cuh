@@ -6,6 +6,7 @@
 // no waiting), so small lattices and the tail of large ones share the GPU.
 #pragma once
 
+#include "dslash_kernel.cuh"
 #include "dslash_site.cuh"
 #include "tune.cuh"
 
@@ -86,8 +87,158 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
     grid_finish(a.red, a.nlat * a.nrhs, a.pstride, [&](int q) { return a.lat[q / a.nrhs].tiles_x; });
 }
 
+// The multi-lattice form of the rhs-per-warp kernel (k_dslash_rw): a tile is (lattice,
+// 32 sites, RT*NRT right-hand sides); a block of 32 x RT threads walks the tiles.  Per tile,
+// warp w loads and rebuilds the links of hop w (w + RT, ...) into shared memory, then each
+// thread applies them to its NRT right-hand sides of one site.  A reduction needs no block
+// sum: every warp owns its right-hand sides, so each warp stores its own partials (column
+// = the tile's site block).  FP32 vectors.
+template <lq_prec GP, int R, int RT, int NRT>
+__global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a) {
+  using L = LinkT<GP, R>;
+  using VT = VecT<LQ_F32>;
+  __shared__ float2 sU[8][9][32];
+  __shared__ int sN[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 1-D block of 32 x RT threads
+  constexpr int TR = RT * NRT;                // right-hand sides per tile
+  const int nty = (a.nrhs + TR - 1) / TR;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    int l = 0;
+    while (l + 1 < a.nlat && tile >= a.lat[l + 1].tile0) ++l;
+    const MLat& Lt = a.lat[l];
+    const Geom& G = Lt.G;
+    const int tl = tile - Lt.tile0;
+    const int ty = tl % nty, tx = tl / nty;
+    const int rhs0 = ty * TR + w * NRT;       // this warp's first right-hand side
+    bool skip = false;                        // uniform over the block: the whole tile
+    if (a.skip_state) {
+      skip = true;
+      for (int r = ty * TR; r < ty * TR + TR && r < a.nrhs; ++r) {
+        const CGScalars& c = a.skip_state[l * a.nrhs + r];
+        skip &= (a.skip_mode == SKIP_DONE) ? (c.done != 0) : (c.active == 0);
+      }
+    }
+    const int cb = tx * 32 + lane;
+    double part[NRT];
+#pragma unroll
+    for (int r = 0; r < NRT; ++r) part[r] = 0.0;
+    if (!skip) {
+      const int cbc = cb < G.Vh ? cb : G.Vh - 1;
+      const int xh = cbc % G.Lxh;
+      const int row = cbc / G.Lxh;
+      const int y = row % G.Ly;
+      const int zt = row / G.Ly;
+      const int z = zt % G.Lz;
+      const int t = zt / G.Lz;
+      const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+      for (int h = w; h < 8; h += RT) {
+        const int mu = h >> 1;
+        const bool bwd = h & 1;
+        int cbf, cbb;
+        dslash_neighbours(G, mu, x, y, z, t, xh, row, cbf, cbb);
+        const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+        const float sg = ((ephase & 1) ? -1.f : 1.f) * (bwd ? -1.f : 1.f);
+        float u[18];
+        L::load(Lt.gauge + (size_t)(2 * mu + (bwd ? 1 - a.out_par : a.out_par)) * Lt.blk_bytes, G.S,
+                bwd ? cbb : cbc, u);
+        if (R == 12) reconstruct_row2(u);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float er = bwd ? u[6 * j + 2 * i] : u[6 * i + 2 * j];
+            const float ei = bwd ? -u[6 * j + 2 * i + 1] : u[6 * i + 2 * j + 1];
+            sU[h][3 * i + j][lane] = make_float2(sg * er, sg * ei);
+          }
+        sN[h][lane] = bwd ? cbb : cbf;
+      }
+      __syncthreads();
+      if (rhs0 < a.nrhs) {
+        float acc[NRT][6];
+        size_t roff[NRT];
+#pragma unroll
+        for (int r = 0; r < NRT; ++r) roff[r] = (size_t)min(rhs0 + r, a.nrhs - 1) * G.Vh;
+        if constexpr (NRT == 1) {
+          float v[8][6];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) VT::load(Lt.in, roff[0] + sN[h][lane], v[h]);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) acc[0][k] = 0.f;
+#pragma unroll
+          for (int h = 0; h < 8; ++h)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                const float2 e = sU[h][3 * i + j][lane];
+                acc[0][2 * i] = fmaf(e.x, v[h][2 * j], acc[0][2 * i]);
+                acc[0][2 * i] = fmaf(-e.y, v[h][2 * j + 1], acc[0][2 * i]);
+                acc[0][2 * i + 1] = fmaf(e.x, v[h][2 * j + 1], acc[0][2 * i + 1]);
+                acc[0][2 * i + 1] = fmaf(e.y, v[h][2 * j], acc[0][2 * i + 1]);
+              }
+        } else {
+          float2 acc2[NRT / 2][6];
+#pragma unroll
+          for (int p = 0; p < NRT / 2; ++p)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc2[p][k] = make_float2(0.f, 0.f);
+          float v[2][NRT][6];
+#pragma unroll
+          for (int r = 0; r < NRT; ++r) VT::load(Lt.in, roff[r] + sN[0][lane], v[0][r]);
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const int cur = h & 1;
+            if (h + 1 < 8) {
+#pragma unroll
+              for (int r = 0; r < NRT; ++r) VT::load(Lt.in, roff[r] + sN[h + 1][lane], v[cur ^ 1][r]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                const float2 e = sU[h][3 * i + j][lane];
+                const float2 E = make_float2(e.x, e.x), F = make_float2(e.y, e.y), N = make_float2(-e.y, -e.y);
+#pragma unroll
+                for (int p = 0; p < NRT / 2; ++p) {
+                  const float2 vr = make_float2(v[cur][2 * p][2 * j], v[cur][2 * p + 1][2 * j]);
+                  const float2 vi = make_float2(v[cur][2 * p][2 * j + 1], v[cur][2 * p + 1][2 * j + 1]);
+                  acc2[p][2 * i] = __ffma2_rn(E, vr, acc2[p][2 * i]);
+                  acc2[p][2 * i] = __ffma2_rn(N, vi, acc2[p][2 * i]);
+                  acc2[p][2 * i + 1] = __ffma2_rn(E, vi, acc2[p][2 * i + 1]);
+                  acc2[p][2 * i + 1] = __ffma2_rn(F, vr, acc2[p][2 * i + 1]);
+                }
+              }
+          }
+#pragma unroll
+          for (int p = 0; p < NRT / 2; ++p)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+              acc[2 * p][k] = acc2[p][k].x;
+              acc[2 * p + 1][k] = acc2[p][k].y;
+            }
+        }
+        if (cb < G.Vh)
+          dslash_epilogue<LQ_F32, NRT, 1>(acc, Lt.out, Lt.w1, Lt.a1, Lt.w2, Lt.a2, a.c, a.reduce, G.Vh, a.nrhs,
+                                          rhs0, cb, 0, part);
+      }
+    }
+    if (a.reduce != RED_NONE && rhs0 < a.nrhs) {
+#pragma unroll
+      for (int r = 0; r < NRT; ++r) {
+        const double sum = warp_sum(part[r]);
+        if (lane == 0 && rhs0 + r < a.nrhs)
+          a.red.partials[(size_t)(l * a.nrhs + rhs0 + r) * a.pstride + tx] = sum;
+      }
+    }
+    __syncthreads();   // shared memory is rewritten by the next tile
+  }
+  if (a.reduce != RED_NONE)
+    grid_finish(a.red, a.nlat * a.nrhs, a.pstride, [&](int q) { return a.lat[q / a.nrhs].tiles_x; });
+}
+
 // Launch-shape helpers -----------------------------------------------------------------
 inline bool dslash_multi_shape_ok(int tile, int tps) {
+  if (tps == kTpsRhsWarps) return tile >= 2 && tile <= 16;   // with the block: dslash_rw_shape_ok
   return (tile == 1 || tile == 2 || tile == 4 || tile == 8) && (tps == 1 || tps == 2 || tps == 4);
 }
 
@@ -97,11 +248,43 @@ inline int multi_tiles(MultiKArgs& a, int block, int tile, int tps) {
   const int ty = (a.nrhs + tile - 1) / tile;
   for (int l = 0; l < a.nlat; ++l) {
     a.lat[l].tile0 = t0;
-    a.lat[l].tiles_x = (int)(((long long)a.lat[l].G.Vh * tps + block - 1) / block);
+    a.lat[l].tiles_x = tps == kTpsRhsWarps ? (a.lat[l].G.Vh + 31) / 32
+                                           : (int)(((long long)a.lat[l].G.Vh * tps + block - 1) / block);
     t0 += a.lat[l].tiles_x * ty;
   }
   a.ntiles = t0;
   return t0;
+}
+
+template <lq_prec GP, int R, int RT, int NRT>
+static cudaError_t launch_multi_rw_inst(MultiKArgs a, int num_sms, cudaStream_t s) {
+  multi_tiles(a, 32 * RT, RT * NRT, kTpsRhsWarps);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_multi_rw<GP, R, RT, NRT>, 32 * RT, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = num_sms * per_sm;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid < 1) return cudaSuccess;
+  k_dslash_multi_rw<GP, R, RT, NRT><<<grid, 32 * RT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <lq_prec GP, int R>
+static cudaError_t launch_multi_rw(const MultiKArgs& a, int block, int tile, int num_sms, cudaStream_t s) {
+  if (!dslash_rw_shape_ok(block, tile)) return cudaErrorInvalidValue;
+  const int rt = block / 32, nrt = tile / rt;
+  switch (rt * 8 + nrt) {
+    case 2 * 8 + 1: return launch_multi_rw_inst<GP, R, 2, 1>(a, num_sms, s);
+    case 2 * 8 + 2: return launch_multi_rw_inst<GP, R, 2, 2>(a, num_sms, s);
+    case 2 * 8 + 4: return launch_multi_rw_inst<GP, R, 2, 4>(a, num_sms, s);
+    case 4 * 8 + 1: return launch_multi_rw_inst<GP, R, 4, 1>(a, num_sms, s);
+    case 4 * 8 + 2: return launch_multi_rw_inst<GP, R, 4, 2>(a, num_sms, s);
+    case 4 * 8 + 4: return launch_multi_rw_inst<GP, R, 4, 4>(a, num_sms, s);
+    case 8 * 8 + 1: return launch_multi_rw_inst<GP, R, 8, 1>(a, num_sms, s);
+    case 8 * 8 + 2: return launch_multi_rw_inst<GP, R, 8, 2>(a, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <lq_prec GP, int R, lq_prec VP, int NR, int TPS>
@@ -120,6 +303,10 @@ static cudaError_t launch_multi_inst(MultiKArgs a, int block, int num_sms, cudaS
 
 template <lq_prec GP, int R, lq_prec VP>
 static cudaError_t launch_multi_shape(const MultiKArgs& a, int block, int tile, int tps, int num_sms, cudaStream_t s) {
+  if (tps == kTpsRhsWarps) {
+    if constexpr (GP != LQ_F64 && VP == LQ_F32) return launch_multi_rw<GP, R>(a, block, tile, num_sms, s);
+    else return cudaErrorInvalidValue;
+  }
   switch (tile * 8 + tps) {
     case 1 * 8 + 1: return launch_multi_inst<GP, R, VP, 1, 1>(a, block, num_sms, s);
     case 1 * 8 + 2: return launch_multi_inst<GP, R, VP, 1, 2>(a, block, num_sms, s);

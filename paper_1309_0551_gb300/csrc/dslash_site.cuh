@@ -156,6 +156,47 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
   if constexpr (std::is_same<T, float>::value && NR % 2 == 0) {
     dslash_hops_pairs<GP, R, VP, NR, TPS>(gauge, blk_bytes, G, out_par, in, rhs_stride, nrhs, rhs0, cb, sub, x, y,
                                           z, t, xh, row, acc);
+  } else if constexpr (std::is_same<T, double>::value) {
+    // FP64 runs at the FP64 ALU's rate on GB300, so every FMA counts: both hops of a
+    // direction go into one temporary, U v_f - U^dag v_b (the minus as an operand sign),
+    // which is scaled by eta once: 78 FMAs per direction and rhs instead of 84.
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int mu = sub * DPT + j;
+      int cbf, cbb;
+      dslash_neighbours(G, mu, x, y, z, t, xh, row, cbf, cbb);
+      const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
+      const T eta = (ephase & 1) ? T(-1) : T(1);
+      T tmp[NR][6];
+      T u[18];
+      L::load(gauge + (size_t)(2 * mu + out_par) * blk_bytes, G.S, cb, u);
+      if (R == 12) reconstruct_row2(u);
+      {
+        T v[NR][6];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbf, v[r]);
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (rhs0 + r < nrhs) mat_vec_set(u, v[r], tmp[r]);
+      }
+      L::load(gauge + (size_t)(2 * mu + opar) * blk_bytes, G.S, cbb, u);
+      if (R == 12) reconstruct_row2(u);
+      {
+        T v[NR][6];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbb, v[r]);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (rhs0 + r < nrhs) {
+            adj_mat_vec_sub(u, v[r], tmp[r]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[r][k] = fma(eta, tmp[r][k], acc[r][k]);
+          }
+        }
+      }
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {

@@ -154,6 +154,9 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// The block-wide helpers below (block_reduce, block_total, block_sum_store, grid_finish)
+// take threadIdx.x as the thread's index in the block: they need one-dimensional blocks.
+//
 // Every thread of the block calls this with its NR per-rhs contributions (rhs0 + r).
 // Partials go to red.partials[rhs][bx] (bx < nbx: the block's column); the last block of
 // the grid to arrive sums them in column order (deterministic for a given launch shape)

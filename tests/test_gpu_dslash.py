@@ -153,3 +153,30 @@ def test_rhs_warp_kernel(lq, gp, recon, block, tile, nrhs, monkeypatch):
             assert rel_l2(got[k], ref[k]) < store_tolerance("f32")
     if tile <= nrhs:
         assert ctx.tune_report() == ""      # the forced shape was taken: nothing was tuned
+
+
+@pytest.mark.parametrize("gp,recon", [("f32", 12), ("bf16", 18)])
+@pytest.mark.parametrize("block,tile", [(64, 2), (128, 8), (256, 8), (64, 8)])
+@pytest.mark.parametrize("nrhs", [3, 8])
+def test_multi_rhs_warp_kernel(lq, gp, recon, block, tile, nrhs, monkeypatch):
+    """The multi-lattice rhs-per-warp kernel, forced through the shape override, on four
+    lattices of different sizes (half volumes 128, 240, 2048 and 8: partial 32-site blocks
+    and a lattice smaller than one block)."""
+    import torch
+    monkeypatch.setenv("LQCD_DSLASH_SHAPE", f"{block},{tile},8")
+    ctx = lq.Context(0)
+    dims_list = [(4, 4, 4, 4), (6, 4, 2, 10), (8, 8, 8, 8), (2, 2, 2, 2)]
+    Us, ins, outs, refs = [], [], [], []
+    for i, dims in enumerate(dims_list):
+        U = synth.gauge_field(dims, "haar", seed=160 + i)
+        chi = synth.fermion_field(dims, nrhs, seed=170 + i)
+        Us.append(lq.lq_gauge_pack(ctx, dims, torch.from_numpy(U).cuda(), gp, recon))
+        ins.append(to_device_vec(chi, "f32"))
+        outs.append(empty_vec(chi.shape, "f32"))
+        refs.append(odslash.dslash_eo_multi(quantize_links(U, gp, recon), from_device_vec(ins[-1]), dims, 0))
+    lq.dslash_eo_multi(ctx, Us, ins, outs, 0, nrhs)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, refs):
+        assert rel_l2(from_device_vec(o), r) < store_tolerance("f32")
+    if tile <= nrhs:
+        assert ctx.tune_report() == ""      # the forced shape was taken: nothing was tuned
