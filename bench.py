@@ -45,7 +45,8 @@ NCU_TRAFFIC = {
     # (block 128, grid 512): 39,350,016 + 3,584 B (profiles/k_dslash_f32_18_16c32.md)
     "f32/18/f32/16x16x16x32/1": (39353600, "a025b9b228373f94"),
 }
-KERNEL_SOURCES = ("paper_1309_0551_gb300/csrc/dslash_kernel.cuh",
+KERNEL_SOURCES = ("paper_1309_0551_gb300/csrc/dslash_args.cuh",
+                  "paper_1309_0551_gb300/csrc/dslash_kernel.cuh",
                   "paper_1309_0551_gb300/csrc/dslash_site.cuh",
                   "paper_1309_0551_gb300/csrc/lqcd_internal.cuh",
                   "paper_1309_0551_gb300/csrc/tune.cuh")

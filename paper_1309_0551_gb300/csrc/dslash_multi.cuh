@@ -6,7 +6,7 @@
 // no waiting), so small lattices and the tail of large ones share the GPU.
 #pragma once
 
-#include "dslash_kernel.cuh"
+#include "dslash_rw.cuh"
 #include "dslash_site.cuh"
 #include "tune.cuh"
 
