@@ -36,6 +36,9 @@ DIMS = (16, 16, 16, 32)
 APPS = 100                 # Dslash applications per step
 FLOPS_PER_SITE = 570
 BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+# GB300's nominal FP64 rate, 1.25 TFLOP/s (about two FP64 FMAs per SM and clock: 152 SMs at
+# 2.07 GHz): the denominator of the FP64 kernels' ALU roofline.
+FP64_PEAK_GFLOPS = 1250.0
 
 # DRAM bytes per k_dslash launch from the ncu capture summarised under profiles/ (key:
 # storage format), with the hash of the kernel sources it was taken on.  A changed kernel
@@ -469,6 +472,12 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
     g = GraphStep(torch, lambda ss: [lq.su3_mul_batch(ctx, Ad, Bd, Cd, 1024, 0, 0, None, ss[0]) for _ in range(20)] and 20, 1)
     ms, launches, _ = time_steps(torch, g, 5, 2, stream)
     out["su3_mul/f64/1024_pairs_us"] = round(ms * 1000.0 / launches, 2)
+    # FP64 kernels are bound by GB300's FP64 ALU, not by HBM: their roofline is the FP64
+    # peak (algorithmic flops, the same counts as "gflops")
+    for k, v in out.items():
+        if isinstance(v, dict) and "/f64/" in f"/{k}/":
+            v["bound"] = "fp64_alu"
+            v["alu_frac"] = round(v["gflops"] / FP64_PEAK_GFLOPS, 3)
     return out
 
 
