@@ -274,8 +274,11 @@ __global__ void __launch_bounds__(kBlas) k_seg_xpay(const void* r, void* p, cons
   }
 }
 
+// dst = src for every system (mask NULL) or for the systems with mask[q].ru set; ||dst||^2
+// of those systems -> FIN_STORE (0 for the others).
 template <lq_prec VS, lq_prec VD>
-__global__ void __launch_bounds__(kBlas) k_seg_convert(const void* src, void* dst, const SegArgs g, Reducer red) {
+__global__ void __launch_bounds__(kBlas) k_seg_convert(const void* src, void* dst, const SegArgs g, Reducer red,
+                                                       const CGScalars* mask) {
   using Sv = VecT<VS>;
   using Dv = VecT<VD>;
   for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(kBlas) k_seg_convert(const void* src, void* ds
     seg_locate(g, tile, q, base, chunk, Vh, l);
     const int i = chunk * kBlas + threadIdx.x;
     double acc[1] = {0.0};
-    if (i < Vh) {
+    if (i < Vh && (!mask || mask[q].ru)) {
       typename Sv::real a[6];
       typename Dv::real b[6];
       Sv::load(src, base + i, a);
@@ -426,20 +429,20 @@ lq_status batch_iteration_dslash(Solver& S) {
 
 // skip_done: leave out the lattices whose systems have all met the tolerance already
 // (their residual and norm entries are then not rewritten).
-lq_status batch_true_residual(Solver& S, bool skip_done) {
+lq_status batch_true_residual(Solver& S, int skip_mode) {
   const Batch& B = *S.batch;
   const lq_gauge* g0 = B.hi[0];
   MultiKArgs d = multi_args(S, true, 1, S.x, S.thi);
-  if (skip_done) {
+  if (skip_mode) {
     d.skip_state = S.sc;
-    d.skip_mode = SKIP_DONE;
+    d.skip_mode = skip_mode;
   }
   lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, LQ_F64, B.key_hi, S.s);
   if (st) return st;
   MultiKArgs e = multi_args(S, true, 0, S.thi, S.rhi, S.b, S.x);
-  if (skip_done) {
+  if (skip_mode) {
     e.skip_state = S.sc;
-    e.skip_mode = SKIP_DONE;
+    e.skip_mode = skip_mode;
   }
   for (int l = 0; l < B.nlat; ++l) {
     e.lat[l].a1 = 1.0;
@@ -529,8 +532,10 @@ lq_status iteration(Solver& S) {
 }
 
 // r_hi = b - M x_hi in FP64 and ||r_hi||^2 -> result (FIN_STORE).
-lq_status true_residual(Solver& S, bool skip_done = false) {
-  if (S.batch) return batch_true_residual(S, skip_done);
+// r_hi = b - M x_hi in FP64 with ||r_hi||^2 -> result.  Batched, `skip_mode` (SKIP_DONE,
+// SKIP_NO_RU) leaves out the lattice tiles whose systems are all skipped.
+lq_status true_residual(Solver& S, int skip_mode = 0) {
+  if (S.batch) return batch_true_residual(S, skip_mode);
   DslashArgs d;
   d.U = S.Uhi;
   d.in = S.x;
@@ -569,13 +574,15 @@ lq_status fold_x(Solver& S) {
   return LQ_OK;
 }
 
-// r_lo = round(r_hi) with ||r_lo||^2 -> result.
-lq_status replace_residual(Solver& S) {
+// r_lo = round(r_hi) with ||r_lo||^2 -> result; batched with `masked`: only the systems
+// whose ru flag is set.
+lq_status replace_residual(Solver& S, bool masked = false) {
   Reducer red = S.reducer(FIN_STORE);
   if (S.batch) {
     const Batch& B = *S.batch;
-    if (S.mixed) k_seg_convert<LQ_F64, LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red);
-    else k_seg_convert<LQ_F64, LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red);
+    const CGScalars* mask = masked ? S.sc : nullptr;
+    if (S.mixed) k_seg_convert<LQ_F64, LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red, mask);
+    else k_seg_convert<LQ_F64, LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red, mask);
     LQ_CHECK_LAUNCH(S.ctx, "k_seg_convert");
     return LQ_OK;
   }
@@ -590,7 +597,7 @@ lq_status replace_residual(Solver& S) {
 lq_status copy_source(Solver& S) {
   Reducer red = S.reducer(FIN_STORE);
   if (S.batch) {
-    k_seg_convert<LQ_F64, LQ_F64><<<S.batch->seg_grid, kBlas, 0, S.s>>>(S.b, S.rhi, S.batch->seg, red);
+    k_seg_convert<LQ_F64, LQ_F64><<<S.batch->seg_grid, kBlas, 0, S.s>>>(S.b, S.rhi, S.batch->seg, red, nullptr);
     LQ_CHECK_LAUNCH(S.ctx, "k_seg_convert(b)");
     return LQ_OK;
   }
@@ -692,7 +699,8 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
 
   GraphHolder graph;
   const int block = P.check_every > 0 ? P.check_every : 20;
-  int total = 0, since = 0, restarts_left = 8;
+  int total = 0, restarts_left = 8;
+  std::vector<int> since(n, 0);   // inner iterations since each system's last reliable update
   bool first = true;
   while (true) {
     bool any_active = false;
@@ -724,37 +732,61 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
         LQ_CUDA(ctx, cudaGraphLaunch(graph.e, S.s));
       }
       total += block;
-      since += block;
+      for (int i = 0; i < n; ++i) since[i] += block;
       st = sync_scalars(S);
       if (st) return st;
     }
-    // ---- decide on a reliable update
+    // ---- decide on reliable updates, system by system
+    std::vector<int> due(n, 0);
     bool need = false;
     for (int i = 0; i < n; ++i) {
       const CGScalars& c = S.sc_host[i];
       if (!isfinite(c.rr)) return lq_fail(ctx, LQ_ERR_NUMERIC, "residual of rhs %d became NaN/Inf", i);
       if (done[i]) continue;
-      if (!c.active) need = true;  // apparent convergence: verify in FP64
-      if (S.mixed && (since >= P.reliable_every || c.rr < P.delta * P.delta * c.rhi2)) need = true;
+      if (!c.active) due[i] = 1;  // apparent convergence: verify in FP64
+      if (S.mixed && (since[i] >= P.reliable_every || c.rr < P.delta * P.delta * c.rhi2)) due[i] = 1;
+      need |= due[i] != 0;
     }
     if (!need) continue;
-    st = fold_x(S);
+    // The right-hand sides of one lattice take the update together, as in a single-lattice
+    // solve (where one FP64 launch computes them all anyway); updating only the systems
+    // whose own trigger fired was measured to stall BF16 inner solves, which rely on the
+    // updates the other right-hand sides set off.  A batched solve leaves the lattices
+    // without a due system alone: its FP64 launches skip their tiles (SKIP_NO_RU) and the
+    // replacement does not touch their iteration.
+    {
+      const int nlat = S.batch ? S.batch->nlat : 1;
+      const int per = n / nlat;   // systems are (lattice, rhs), lattice-major
+      for (int l = 0; l < nlat; ++l) {
+        bool any = false;
+        for (int k = 0; k < per; ++k) any |= due[l * per + k] != 0;
+        for (int k = 0; k < per; ++k) due[l * per + k] = any && !done[l * per + k];
+      }
+    }
+    for (int i = 0; i < n; ++i) S.sc_host[i].ru = due[i];
+    if (S.batch) {
+      st = push_scalars(S);
+      if (st) return st;
+    }
+    st = fold_x(S);              // exact for every system: x_hi + x_lo keeps its value
     if (st) return st;
-    st = true_residual(S, /*skip_done=*/true);
+    st = true_residual(S, S.batch ? SKIP_NO_RU : SKIP_DONE);
     if (st) return st;
     std::vector<double> rhi2;
     st = read_result(S, rhi2);
     if (st) return st;
-    st = replace_residual(S);
+    st = replace_residual(S, /*masked=*/S.batch != nullptr);
     if (st) return st;
     std::vector<double> rlo2;
     st = read_result(S, rlo2);
     if (st) return st;
-    since = 0;
     bool restarted = false;
     for (int i = 0; i < n; ++i) {
       CGScalars& c = S.sc_host[i];
+      c.ru = 0;
       if (done[i]) { c.active = 0; continue; }
+      if (!due[i]) continue;
+      since[i] = 0;
       updates[i] += 1;
       if (!isfinite(rhi2[i])) return lq_fail(ctx, LQ_ERR_NUMERIC, "true residual of rhs %d is NaN/Inf", i);
       if (rhi2[i] <= tol2 * bb[i]) {

@@ -11,7 +11,13 @@
 #include "tune.cuh"
 
 constexpr int kMaxLat = 16;
-enum { SKIP_INACTIVE = 1, SKIP_DONE = 2 };
+enum { SKIP_INACTIVE = 1, SKIP_DONE = 2, SKIP_NO_RU = 3 };
+
+// A system is skipped when it is inactive (SKIP_INACTIVE), done (SKIP_DONE), or does not
+// take the reliable update under way (SKIP_NO_RU).
+__device__ __forceinline__ bool system_skipped(const CGScalars& c, int mode) {
+  return mode == SKIP_DONE ? c.done != 0 : mode == SKIP_NO_RU ? c.ru == 0 : c.active == 0;
+}
 
 struct MLat {
   const char* gauge;  // packed links of this lattice
@@ -32,7 +38,7 @@ struct MultiKArgs {
   int reduce;
   size_t pstride;     // partials row stride (columns per (lattice, rhs) row)
   const CGScalars* skip_state;  // optional per-system state: tiles whose systems are all
-  int skip_mode;                // inactive (SKIP_INACTIVE) or all done (SKIP_DONE) are skipped
+  int skip_mode;                // skipped (system_skipped) are not computed
   Reducer red;        // rows q = l * nrhs + rhs
   MLat lat[kMaxLat];
 };
@@ -54,7 +60,7 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
       skip = true;
       for (int r = 0; r < NR && rhs0 + r < a.nrhs; ++r) {
         const CGScalars& c = a.skip_state[l * a.nrhs + rhs0 + r];
-        skip &= (a.skip_mode == SKIP_DONE) ? (c.done != 0) : (c.active == 0);
+        skip &= system_skipped(c, a.skip_mode);
       }
     }
     double part[NR];
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a)
       skip = true;
       for (int r = ty * TR; r < ty * TR + TR && r < a.nrhs; ++r) {
         const CGScalars& c = a.skip_state[l * a.nrhs + r];
-        skip &= (a.skip_mode == SKIP_DONE) ? (c.done != 0) : (c.active == 0);
+        skip &= system_skipped(c, a.skip_mode);
       }
     }
     const int cb = tx * 32 + lane;

@@ -118,7 +118,7 @@ struct CGScalars {
   int active;     // 1 while iterating
   int iters;      // iterations done while active
   int done;       // set by the host once the FP64 true residual met the tolerance
-  int pad;
+  int ru;         // set by the host: this system takes the reliable update now (batched solve)
 };
 
 // FIN_DEFER: the blocks only store their partials; a later kernel sums them (block_total).
