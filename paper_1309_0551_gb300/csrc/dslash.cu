@@ -99,7 +99,10 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   // w1 or w2 and their reductions only store totals or alpha = rr / total.
   DslashKArgs plain = k;
   plain.pdl = 0;
-  if (a.reduce == RED_NONE) {
+  // a finisher that is not idempotent (FIN_BETA advances the CG state) is never repeated
+  const bool tune_as_is = a.reduce != RED_NONE && a.red && a.red->finisher != FIN_BETA;
+  if (!tune_as_is) {
+    plain.reduce = RED_NONE;
     plain.w1 = plain.w2 = nullptr;
     plain.a1 = plain.a2 = 0.0;
     plain.c = 1.0;
@@ -228,10 +231,13 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
   // tuned as itself (its cost depends on the shape; the solvers never let out alias w1 or
   // w2, and their finishers only store totals or alpha = rr / total).
   MultiKArgs plain = a;
-  if (a.reduce == RED_NONE) {
+  // a finisher that is not idempotent (FIN_BETA advances the CG state) is never repeated
+  const bool tune_as_is = a.reduce != RED_NONE && a.red.finisher != FIN_BETA;
+  if (!tune_as_is) {
     for (int l = 0; l < a.nlat; ++l) plain.lat[l].w1 = plain.lat[l].w2 = nullptr;
     plain.c = 1.0;
     plain.skip_state = nullptr;
+    plain.reduce = RED_NONE;
   }
   const bool rw_ok = gp != LQ_F64 && vp == LQ_F32 && a.nrhs >= 2;
   TuneEntry pick;
