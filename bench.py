@@ -325,6 +325,43 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
                                        "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
         del gauges, ins, ts, outs
         torch.cuda.empty_cache()
+    # FP32-18 with one copy of links and vectors (40.9 MB, L2-resident): the L2-warm number
+    # beside the flushed ones above; "frac" is still against the HBM copy bandwidth
+    sb = site_bytes("f32", 18, "f32")
+    gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 18, "f32", 1)
+    K = 2 * nstreams
+    gauges, ins, ts, outs = gauges * K, ins * K, [ts[0]] * K, [outs[0]] * K
+    g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
+    ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+    del g
+    us = ms * 1000.0 / launches
+    gbs = Vh * sb / us / 1e3
+    out["f32/18/f32/l2_warm"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+                                 "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb,
+                                 "ring": 1}
+    del gauges, ins, ts, outs
+    torch.cuda.empty_cache()
+    # FP32-18 at 32^4 (327 MB per copy: every launch reads its links from HBM)
+    import synth
+    d4 = (32, 32, 32, 32)
+    Vh4 = synth.volume(d4) // 2
+    U4 = torch.from_numpy(synth.gauge_field(d4, "near_identity", seed=3, eps=0.3)).cuda()
+    for prec, recon in (("f32", 18), ("f32", 12)):
+        sb = site_bytes(prec, recon, "f32")
+        K = ring_size(Vh4 * sb, l2, nstreams)
+        gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, "f32", K)
+        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
+        ms, launches, _ = time_steps(torch, g, 5, 3, stream)
+        del g
+        us = ms * 1000.0 / launches
+        gbs = Vh4 * sb / us / 1e3
+        out[f"{prec}/{recon}/f32/32x32x32x32"] = {"gflops": round(Vh4 * FLOPS_PER_SITE / us / 1e3, 1),
+                                                  "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                                                  "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+        del gauges, ins, ts, outs
+        torch.cuda.empty_cache()
+    del U4
+    torch.cuda.empty_cache()
     # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
     for prec in ("f32", "bf16"):
         vec = "f32" if prec == "f32" else "bf16"
@@ -361,7 +398,6 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
         del fats, lngs, ins, ts, outs, itmp, iout
         torch.cuda.empty_cache()
     # Wilson hopping term through half Wilson vectors (8 hops, 1320 flops per site)
-    import synth
     for prec, recon in (("f32", 18), ("f32", 12), ("bf16", 12), ("f64", 18)):
         vec = "f64" if prec == "f64" else "f32"
         sb = 8 * recon * BYTES[prec] + 2 * 24 * BYTES[vec]

@@ -86,6 +86,29 @@ def test_full_size_16c32_sampled(lq, ctx, gp, recon, vp):
         assert rel_l2(got[0][sites], ref) < store_tolerance(vp)
 
 
+@pytest.fixture(scope="module")
+def field_32c4():
+    return synth.gauge_field((32, 32, 32, 32), "near_identity", seed=3, eps=0.3)
+
+
+@pytest.mark.parametrize("gp,recon", [("f32", 18), ("f32", 12)])
+def test_full_size_32c4_sampled(lq, ctx, field_32c4, gp, recon):
+    """The 32^4 near-identity (eps 0.3) lines of the benchmark (every launch reads its
+    links from HBM), checked on 200 sampled output sites per parity, the last site
+    included."""
+    dims = (32, 32, 32, 32)
+    U = field_32c4
+    Uq = quantize_links(U, gp, recon)
+    rs = synth.rng(68)
+    for parity in (0, 1):
+        chi = synth.fermion_field(dims, 1, seed=69 + parity)
+        got, chi_q = _run(lq, ctx, U, dims, gp, recon, "f32", chi, parity)
+        sites = np.sort(rs.choice(chi.shape[1], 200, replace=False))
+        sites[-1] = chi.shape[1] - 1
+        ref = odslash.dslash_eo_sites(Uq, chi_q[0], dims, parity, sites)
+        assert rel_l2(got[0][sites], ref) < store_tolerance("f32")
+
+
 def test_invalid_arguments(lq, ctx):
     import torch
     dims = (4, 4, 4, 4)
