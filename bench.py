@@ -85,6 +85,8 @@ def parse():
     p.add_argument("--streams", type=int, default=4,
                    help="independent applications in flight (graph branches)")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--variants", default="all",
+                   help="comma-separated variant groups: formats, l2_warm, 32c4, improved, wilson, multi_rhs, su3")
     p.add_argument("--no-cg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cg-maxiter", type=int, default=20000,
@@ -304,210 +306,224 @@ def cpu_baseline(dims, seconds=12.0):
                       f"{'x'.join(map(str, dims))} lattice ({dt:.1f} s)"}
 
 
-def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams):
+def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all"):
+    """The per-format, operator and SU(3)-batch lines; `groups` (comma-separated, or "all")
+    picks among formats, l2_warm, 32c4, improved, wilson, multi_rhs, su3."""
+    import synth
+    sel = set(groups.split(","))
+
+    def want(name):
+        return "all" in sel or name in sel
+
     out = {}
     forms = [("f64", 18, "f64"), ("f64", 12, "f64"), ("f32", 18, "f32"), ("f32", 12, "f32"),
              ("bf16", 18, "bf16"), ("bf16", 12, "bf16"), ("f16", 12, "f16")]
     peak, _ = measured_peak()
     Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
-    for prec, recon, vec in forms:
-        sb = site_bytes(prec, recon, vec)
-        K = ring_size(Vh * sb, l2, nstreams)
-        gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K)
-        vc = lq.PREC[vec]
-        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
-        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-        del g
-        us = ms * 1000.0 / launches
-        gbs = Vh * sb / us / 1e3
-        out[f"{prec}/{recon}/{vec}"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1),
-                                       "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
-                                       "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
-        del gauges, ins, ts, outs
-        torch.cuda.empty_cache()
-    # FP32-18 with one copy of links and vectors (40.9 MB, L2-resident): the L2-warm number
-    # beside the flushed ones above; "frac" is still against the HBM copy bandwidth
-    sb = site_bytes("f32", 18, "f32")
-    gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 18, "f32", 1)
-    K = 2 * nstreams
-    gauges, ins, ts, outs = gauges * K, ins * K, [ts[0]] * K, [outs[0]] * K
-    g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
-    ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-    del g
-    us = ms * 1000.0 / launches
-    gbs = Vh * sb / us / 1e3
-    out["f32/18/f32/l2_warm"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
-                                 "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb,
-                                 "ring": 1}
-    del gauges, ins, ts, outs
-    torch.cuda.empty_cache()
-    # FP32-18 at 32^4 (327 MB per copy: every launch reads its links from HBM)
-    import synth
-    d4 = (32, 32, 32, 32)
-    Vh4 = synth.volume(d4) // 2
-    U4 = torch.from_numpy(synth.gauge_field(d4, "near_identity", seed=3, eps=0.3)).cuda()
-    for prec, recon in (("f32", 18), ("f32", 12)):
-        sb = site_bytes(prec, recon, "f32")
-        K = ring_size(Vh4 * sb, l2, nstreams)
-        gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, "f32", K)
+    if want("formats"):
+        for prec, recon, vec in forms:
+            sb = site_bytes(prec, recon, vec)
+            K = ring_size(Vh * sb, l2, nstreams)
+            gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K)
+            vc = lq.PREC[vec]
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
+            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = Vh * sb / us / 1e3
+            out[f"{prec}/{recon}/{vec}"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1),
+                                           "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                                           "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+            del gauges, ins, ts, outs
+            torch.cuda.empty_cache()
+    if want("l2_warm"):
+        # FP32-18 with one copy of links and vectors (40.9 MB, L2-resident): the L2-warm number
+        # beside the flushed ones above; "frac" is still against the HBM copy bandwidth
+        sb = site_bytes("f32", 18, "f32")
+        gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 18, "f32", 1)
+        K = 2 * nstreams
+        gauges, ins, ts, outs = gauges * K, ins * K, [ts[0]] * K, [outs[0]] * K
         g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
-        ms, launches, _ = time_steps(torch, g, 5, 3, stream)
+        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
         del g
         us = ms * 1000.0 / launches
-        gbs = Vh4 * sb / us / 1e3
-        out[f"{prec}/{recon}/f32/32x32x32x32"] = {"gflops": round(Vh4 * FLOPS_PER_SITE / us / 1e3, 1),
-                                                  "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
-                                                  "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+        gbs = Vh * sb / us / 1e3
+        out["f32/18/f32/l2_warm"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+                                     "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb,
+                                     "ring": 1}
         del gauges, ins, ts, outs
         torch.cuda.empty_cache()
-    del U4
-    torch.cuda.empty_cache()
-    # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
-    for prec in ("f32", "bf16"):
-        vec = "f32" if prec == "f32" else "bf16"
-        sb = 2 * 8 * 18 * BYTES[prec] + 12 * BYTES[vec]
-        K = ring_size(Vh * sb, l2, nstreams)
-        Ld = torch.empty_like(U_dev)
-        lq.lq_long_links(ctx, DIMS, U_dev, -1.0 / 24, Ld)
-        fats = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, 18) for _ in range(K)]
-        lngs = [lq.lq_gauge_pack(ctx, DIMS, Ld, prec, 18) for _ in range(K)]
-        del Ld
-        _, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 12, vec, 1)
-        ins, ts, outs = ins * K, [ts[0]] * K, [outs[0]] * K
-        vc = lq.PREC[vec]
-
-        def istep(ss, fats=fats, lngs=lngs, ins=ins, vc=vc):
-            h = 0
-            for a in range(20):
-                s_ = ss[a % len(ss)]
-                c, c2 = h % K, (h + 1) % K
-                lq.dslash_eo_improved(ctx, fats[c], lngs[c], ins[c], itmp[a % len(ss)], 1, 1, vc, s_)
-                lq.dslash_eo_improved(ctx, fats[c2], lngs[c2], itmp[a % len(ss)], iout[a % len(ss)], 0, 1, vc, s_)
-                h += 2
-            return 40
-        itmp = [torch.empty_like(ins[0]) for _ in range(nstreams)]
-        iout = [torch.empty_like(ins[0]) for _ in range(nstreams)]
-        g = GraphStep(torch, istep, nstreams)
-        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-        del g
-        us = ms * 1000.0 / launches
-        gbs = Vh * sb / us / 1e3
-        out[f"improved/{prec}/18/{vec}"] = {"gflops": round(Vh * 1146 / us / 1e3, 1), "gbs": round(gbs, 1),
-                                            "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
-                                            "bytes_per_site": sb, "ring": K}
-        del fats, lngs, ins, ts, outs, itmp, iout
-        torch.cuda.empty_cache()
-    # Wilson hopping term through half Wilson vectors (8 hops, 1320 flops per site)
-    for prec, recon in (("f32", 18), ("f32", 12), ("bf16", 12), ("f64", 18)):
-        vec = "f64" if prec == "f64" else "f32"
-        sb = 8 * recon * BYTES[prec] + 2 * 24 * BYTES[vec]
-        K = ring_size(Vh * sb, l2, nstreams)
-        wg = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
-        dt = torch.complex128 if vec == "f64" else torch.complex64
-        host = torch.from_numpy(synth.spinor_field(DIMS, 1, seed=9)).to(dt)
-        wins = [host.cuda() for _ in range(K)]
-        wtmp = [torch.empty_like(wins[0]) for _ in range(nstreams)]
-        wout = [torch.empty_like(wins[0]) for _ in range(nstreams)]
-        vc = lq.PREC[vec]
-
-        def wstep(ss, wg=wg, wins=wins, wtmp=wtmp, wout=wout, vc=vc, K=K):
-            h = 0
-            for a in range(20):
-                s_ = ss[a % len(ss)]
-                c, c2 = h % K, (h + 1) % K
-                lq.dslash_wilson_eo(ctx, wg[c], wins[c], wtmp[a % len(ss)], 1, 1, vc, 1, s_)
-                lq.dslash_wilson_eo(ctx, wg[c2], wtmp[a % len(ss)], wout[a % len(ss)], 0, 1, vc, 1, s_)
-                h += 2
-            return 40
-        g = GraphStep(torch, wstep, nstreams)
-        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-        del g
-        us = ms * 1000.0 / launches
-        gbs = Vh * sb / us / 1e3
-        out[f"wilson/{prec}/{recon}/{vec}"] = {"gflops": round(Vh * 1320 / us / 1e3, 1), "gbs": round(gbs, 1),
-                                               "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
-                                               "bytes_per_site": sb, "ring": K}
-        del wg, wins, wtmp, wout
-        torch.cuda.empty_cache()
-    # multi-RHS Dslash (links loaded once per site for all right-hand sides)
-    for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
-        sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
-        K = ring_size(Vh * sb, l2, nstreams)
-        gauges = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
-        chi = torch.from_numpy(synth.fermion_field(DIMS, nrhs, seed=12)).to(torch.complex64)
-        ins = [chi.cuda() for _ in range(K)]
-        ts = [torch.empty_like(ins[0]) for _ in range(K)]
-        outs = [torch.empty_like(ins[0]) for _ in range(K)]
-
-        def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs):
-            h = 0
-            for a in range(10):
-                s_ = ss[a % len(ss)]
-                c, c2 = h % K, (h + 1) % K
-                lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
-                lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
-                h += 2
-            return 20
-        g = GraphStep(torch, mstep, nstreams)
-        ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-        del g
-        us = ms * 1000.0 / launches
-        gbs = Vh * sb / us / 1e3
-        out[f"multi_rhs/{prec}/{recon}/nrhs{nrhs}"] = {
-            "gflops": round(Vh * nrhs * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
-            "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
-        del gauges, ins, ts, outs
-        torch.cuda.empty_cache()
-    # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
-    n = 4 * 2 * Vh
-    A = torch.from_numpy(synth.haar_su3(synth.rng(9), n))
-    b = torch.from_numpy(synth.complex_gaussian(synth.rng(10), (n, 3)))
-    for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
-        per = n * 30 * BYTES[prec]
-        K = ring_size(per, l2)
-        As = [A.to(dt).cuda() for _ in range(K)]
-        bs = [b.to(dt).cuda() for _ in range(K)]
-        cs = [torch.empty_like(bs[0]) for _ in range(K)]
-        for adj in (0, 1):
-            def step(ss):
-                for i in range(20):
-                    lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[0])
-                return 20
-            g = GraphStep(torch, step, 1)
-            ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+    if want("32c4"):
+        # FP32-18 at 32^4 (327 MB per copy: every launch reads its links from HBM)
+        d4 = (32, 32, 32, 32)
+        Vh4 = synth.volume(d4) // 2
+        U4 = torch.from_numpy(synth.gauge_field(d4, "near_identity", seed=3, eps=0.3)).cuda()
+        for prec, recon in (("f32", 18), ("f32", 12)):
+            sb = site_bytes(prec, recon, "f32")
+            K = ring_size(Vh4 * sb, l2, nstreams)
+            gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, "f32", K)
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
+            ms, launches, _ = time_steps(torch, g, 5, 3, stream)
             del g
             us = ms * 1000.0 / launches
-            gbs = per / us / 1e3
-            out[f"su3_matvec/{prec}/adj{adj}"] = {"gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1),
-                                                  "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
-        del As, bs, cs
-    # mult_su3_nn / an / na over the 4V links (pairs of Haar matrices)
-    B2 = torch.from_numpy(synth.haar_su3(synth.rng(11), n))
-    for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
-        per = n * 54 * BYTES[prec]
-        K = ring_size(per, l2)
-        As = [A.to(dt).cuda() for _ in range(K)]
-        Bs = [B2.to(dt).cuda() for _ in range(K)]
-        Cs = [torch.empty_like(As[0]) for _ in range(K)]
-        for adjA, adjB in ((0, 0), (1, 0), (0, 1)):
-            def step(ss):
-                for i in range(20):
-                    lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[0])
-                return 20
-            g = GraphStep(torch, step, 1)
-            ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+            gbs = Vh4 * sb / us / 1e3
+            out[f"{prec}/{recon}/f32/32x32x32x32"] = {"gflops": round(Vh4 * FLOPS_PER_SITE / us / 1e3, 1),
+                                                      "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                                                      "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+            del gauges, ins, ts, outs
+            torch.cuda.empty_cache()
+        del U4
+        torch.cuda.empty_cache()
+    if want("improved"):
+        # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
+        for prec in ("f32", "bf16"):
+            vec = "f32" if prec == "f32" else "bf16"
+            sb = 2 * 8 * 18 * BYTES[prec] + 12 * BYTES[vec]
+            K = ring_size(Vh * sb, l2, nstreams)
+            Ld = torch.empty_like(U_dev)
+            lq.lq_long_links(ctx, DIMS, U_dev, -1.0 / 24, Ld)
+            fats = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, 18) for _ in range(K)]
+            lngs = [lq.lq_gauge_pack(ctx, DIMS, Ld, prec, 18) for _ in range(K)]
+            del Ld
+            _, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 12, vec, 1)
+            ins, ts, outs = ins * K, [ts[0]] * K, [outs[0]] * K
+            vc = lq.PREC[vec]
+
+            def istep(ss, fats=fats, lngs=lngs, ins=ins, vc=vc):
+                h = 0
+                for a in range(20):
+                    s_ = ss[a % len(ss)]
+                    c, c2 = h % K, (h + 1) % K
+                    lq.dslash_eo_improved(ctx, fats[c], lngs[c], ins[c], itmp[a % len(ss)], 1, 1, vc, s_)
+                    lq.dslash_eo_improved(ctx, fats[c2], lngs[c2], itmp[a % len(ss)], iout[a % len(ss)], 0, 1, vc, s_)
+                    h += 2
+                return 40
+            itmp = [torch.empty_like(ins[0]) for _ in range(nstreams)]
+            iout = [torch.empty_like(ins[0]) for _ in range(nstreams)]
+            g = GraphStep(torch, istep, nstreams)
+            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
             del g
             us = ms * 1000.0 / launches
-            gbs = per / us / 1e3
-            out[f"su3_mul/{prec}/adj{adjA}{adjB}"] = {"gflops": round(n * 198 / us / 1e3, 1), "gbs": round(gbs, 1),
-                                                     "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
-        del As, Bs, Cs
-    # the 1024-pair FP64 product of the 4^4 configuration: latency of one call
-    Ad, Bd = A[:1024].cuda(), B2[:1024].cuda()
-    Cd = torch.empty_like(Ad)
-    g = GraphStep(torch, lambda ss: [lq.su3_mul_batch(ctx, Ad, Bd, Cd, 1024, 0, 0, None, ss[0]) for _ in range(20)] and 20, 1)
-    ms, launches, _ = time_steps(torch, g, 5, 2, stream)
-    out["su3_mul/f64/1024_pairs_us"] = round(ms * 1000.0 / launches, 2)
+            gbs = Vh * sb / us / 1e3
+            out[f"improved/{prec}/18/{vec}"] = {"gflops": round(Vh * 1146 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
+                                                "bytes_per_site": sb, "ring": K}
+            del fats, lngs, ins, ts, outs, itmp, iout
+            torch.cuda.empty_cache()
+    if want("wilson"):
+        # Wilson hopping term through half Wilson vectors (8 hops, 1320 flops per site)
+        for prec, recon in (("f32", 18), ("f32", 12), ("bf16", 12), ("f64", 18)):
+            vec = "f64" if prec == "f64" else "f32"
+            sb = 8 * recon * BYTES[prec] + 2 * 24 * BYTES[vec]
+            K = ring_size(Vh * sb, l2, nstreams)
+            wg = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
+            dt = torch.complex128 if vec == "f64" else torch.complex64
+            host = torch.from_numpy(synth.spinor_field(DIMS, 1, seed=9)).to(dt)
+            wins = [host.cuda() for _ in range(K)]
+            wtmp = [torch.empty_like(wins[0]) for _ in range(nstreams)]
+            wout = [torch.empty_like(wins[0]) for _ in range(nstreams)]
+            vc = lq.PREC[vec]
+
+            def wstep(ss, wg=wg, wins=wins, wtmp=wtmp, wout=wout, vc=vc, K=K):
+                h = 0
+                for a in range(20):
+                    s_ = ss[a % len(ss)]
+                    c, c2 = h % K, (h + 1) % K
+                    lq.dslash_wilson_eo(ctx, wg[c], wins[c], wtmp[a % len(ss)], 1, 1, vc, 1, s_)
+                    lq.dslash_wilson_eo(ctx, wg[c2], wtmp[a % len(ss)], wout[a % len(ss)], 0, 1, vc, 1, s_)
+                    h += 2
+                return 40
+            g = GraphStep(torch, wstep, nstreams)
+            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = Vh * sb / us / 1e3
+            out[f"wilson/{prec}/{recon}/{vec}"] = {"gflops": round(Vh * 1320 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                   "frac": round(gbs / peak, 3), "us_per_half": round(us, 2),
+                                                   "bytes_per_site": sb, "ring": K}
+            del wg, wins, wtmp, wout
+            torch.cuda.empty_cache()
+    if want("multi_rhs"):
+        # multi-RHS Dslash (links loaded once per site for all right-hand sides)
+        for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
+            sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
+            K = ring_size(Vh * sb, l2, nstreams)
+            gauges = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
+            chi = torch.from_numpy(synth.fermion_field(DIMS, nrhs, seed=12)).to(torch.complex64)
+            ins = [chi.cuda() for _ in range(K)]
+            ts = [torch.empty_like(ins[0]) for _ in range(K)]
+            outs = [torch.empty_like(ins[0]) for _ in range(K)]
+
+            def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs):
+                h = 0
+                for a in range(10):
+                    s_ = ss[a % len(ss)]
+                    c, c2 = h % K, (h + 1) % K
+                    lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
+                    lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
+                    h += 2
+                return 20
+            g = GraphStep(torch, mstep, nstreams)
+            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = Vh * sb / us / 1e3
+            out[f"multi_rhs/{prec}/{recon}/nrhs{nrhs}"] = {
+                "gflops": round(Vh * nrhs * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+                "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+            del gauges, ins, ts, outs
+            torch.cuda.empty_cache()
+    if want("su3"):
+        # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
+        n = 4 * 2 * Vh
+        A = torch.from_numpy(synth.haar_su3(synth.rng(9), n))
+        b = torch.from_numpy(synth.complex_gaussian(synth.rng(10), (n, 3)))
+        for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
+            per = n * 30 * BYTES[prec]
+            K = ring_size(per, l2)
+            As = [A.to(dt).cuda() for _ in range(K)]
+            bs = [b.to(dt).cuda() for _ in range(K)]
+            cs = [torch.empty_like(bs[0]) for _ in range(K)]
+            for adj in (0, 1):
+                def step(ss):
+                    for i in range(20):
+                        lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[0])
+                    return 20
+                g = GraphStep(torch, step, 1)
+                ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+                del g
+                us = ms * 1000.0 / launches
+                gbs = per / us / 1e3
+                out[f"su3_matvec/{prec}/adj{adj}"] = {"gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                      "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
+            del As, bs, cs
+        # mult_su3_nn / an / na over the 4V links (pairs of Haar matrices)
+        B2 = torch.from_numpy(synth.haar_su3(synth.rng(11), n))
+        for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
+            per = n * 54 * BYTES[prec]
+            K = ring_size(per, l2)
+            As = [A.to(dt).cuda() for _ in range(K)]
+            Bs = [B2.to(dt).cuda() for _ in range(K)]
+            Cs = [torch.empty_like(As[0]) for _ in range(K)]
+            for adjA, adjB in ((0, 0), (1, 0), (0, 1)):
+                def step(ss):
+                    for i in range(20):
+                        lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[0])
+                    return 20
+                g = GraphStep(torch, step, 1)
+                ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+                del g
+                us = ms * 1000.0 / launches
+                gbs = per / us / 1e3
+                out[f"su3_mul/{prec}/adj{adjA}{adjB}"] = {"gflops": round(n * 198 / us / 1e3, 1), "gbs": round(gbs, 1),
+                                                         "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
+            del As, Bs, Cs
+        # the 1024-pair FP64 product of the 4^4 configuration: latency of one call
+        Ad, Bd = A[:1024].cuda(), B2[:1024].cuda()
+        Cd = torch.empty_like(Ad)
+        g = GraphStep(torch, lambda ss: [lq.su3_mul_batch(ctx, Ad, Bd, Cd, 1024, 0, 0, None, ss[0]) for _ in range(20)] and 20, 1)
+        ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+        out["su3_mul/f64/1024_pairs_us"] = round(ms * 1000.0 / launches, 2)
     # FP64 kernels are bound by GB300's FP64 ALU, not by HBM: their roofline is the FP64
     # peak (algorithmic flops, the same counts as "gflops")
     for k, v in out.items():
@@ -689,7 +705,7 @@ def run_ours(args):
     if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
         U_var = U_dev if dims == DIMS else torch.from_numpy(
             synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)).cuda()
-        extra["variants"] = run_variants(lq, ctx, torch, U_var, l2, stream, args.streams)
+        extra["variants"] = run_variants(lq, ctx, torch, U_var, l2, stream, args.streams, args.variants)
     if rank == 0 and not args.no_cg:
         ctx.set_tuning(1)  # the solvers issue one launch at a time
         extra["cg"] = run_cg(lq, ctx, torch, args.cg_maxiter)
