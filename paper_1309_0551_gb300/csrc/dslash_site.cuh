@@ -64,17 +64,18 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
     dslash_hops_pairs<GP, R, VP, NR, TPS>(gauge, blk_bytes, G, out_par, in, rhs_stride, nrhs, rhs0, cb, sub, x, y,
                                           z, t, xh, row, acc);
   } else if constexpr (std::is_same<T, double>::value) {
-    // FP64 runs at the FP64 ALU's rate on GB300, so every FMA counts: both hops of a
-    // direction go into one temporary, U v_f - U^dag v_b (the minus as an operand sign),
-    // which is scaled by eta once: 78 FMAs per direction and rhs instead of 84.
+    // FP64 runs at the FP64 ALU's rate on GB300, so every FP64 instruction counts.  The
+    // hop's sign (eta forward, -eta backward) is put on the neighbour vector by flipping
+    // its sign bits -- integer XORs, off the FP64 pipe and exact -- and both hops then
+    // accumulate straight into acc: 72 FP64 FMAs per direction and rhs.
+    constexpr unsigned long long kSign = 0x8000000000000000ull;
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
       const int mu = sub * DPT + j;
       int cbf, cbb;
       dslash_neighbours(G, mu, x, y, z, t, xh, row, cbf, cbb);
       const int ephase = (mu == 0) ? 0 : (mu == 1) ? x : (mu == 2) ? x + y : x + y + z;
-      const T eta = (ephase & 1) ? T(-1) : T(1);
-      T tmp[NR][6];
+      const unsigned long long sf = (ephase & 1) ? kSign : 0ull;   // eta < 0
       T u[18];
       L::load(gauge + (size_t)(2 * mu + out_par) * blk_bytes, G.S, cb, u);
       if (R == 12) reconstruct_row2(u);
@@ -84,8 +85,13 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
         for (int r = 0; r < NR; ++r)
           if (rhs0 + r < nrhs) VT::load(in, (size_t)(rhs0 + r) * rhs_stride + cbf, v[r]);
 #pragma unroll
-        for (int r = 0; r < NR; ++r)
-          if (rhs0 + r < nrhs) mat_vec_set(u, v[r], tmp[r]);
+        for (int r = 0; r < NR; ++r) {
+          if (rhs0 + r < nrhs) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[r][k] = __longlong_as_double(__double_as_longlong(v[r][k]) ^ sf);
+            mat_vec_add(u, v[r], acc[r]);
+          }
+        }
       }
       L::load(gauge + (size_t)(2 * mu + opar) * blk_bytes, G.S, cbb, u);
       if (R == 12) reconstruct_row2(u);
@@ -97,9 +103,10 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (rhs0 + r < nrhs) {
-            adj_mat_vec_sub(u, v[r], tmp[r]);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[r][k] = fma(eta, tmp[r][k], acc[r][k]);
+            for (int k = 0; k < 6; ++k)
+              v[r][k] = __longlong_as_double(__double_as_longlong(v[r][k]) ^ (sf ^ kSign));
+            adj_mat_vec_add(u, v[r], acc[r]);
           }
         }
       }

@@ -408,35 +408,30 @@ template <class T> __device__ __forceinline__ void mat_vec_acc(const T* u, const
   }
 }
 
-// out = U v (no scaling: the first product of each chain starts it).
-template <class T> __device__ __forceinline__ void mat_vec_set(const T* u, const T* v, T* out) {
+// acc += U v, accumulated in place (no scaling).
+template <class T> __device__ __forceinline__ void mat_vec_add(const T* u, const T* v, T* acc) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    T re = u[6 * i] * v[0], im = u[6 * i] * v[1];
-    re = fma(-u[6 * i + 1], v[1], re);
-    im = fma(u[6 * i + 1], v[0], im);
 #pragma unroll
-    for (int j = 1; j < 3; ++j) {
-      re = fma(u[6 * i + 2 * j], v[2 * j], re);
-      re = fma(-u[6 * i + 2 * j + 1], v[2 * j + 1], re);
-      im = fma(u[6 * i + 2 * j], v[2 * j + 1], im);
-      im = fma(u[6 * i + 2 * j + 1], v[2 * j], im);
+    for (int j = 0; j < 3; ++j) {
+      acc[2 * i] = fma(u[6 * i + 2 * j], v[2 * j], acc[2 * i]);
+      acc[2 * i] = fma(-u[6 * i + 2 * j + 1], v[2 * j + 1], acc[2 * i]);
+      acc[2 * i + 1] = fma(u[6 * i + 2 * j], v[2 * j + 1], acc[2 * i + 1]);
+      acc[2 * i + 1] = fma(u[6 * i + 2 * j + 1], v[2 * j], acc[2 * i + 1]);
     }
-    out[2 * i] = re;
-    out[2 * i + 1] = im;
   }
 }
 
-// acc -= U^dag v, accumulated in place (negated products: no extra instruction).
-template <class T> __device__ __forceinline__ void adj_mat_vec_sub(const T* u, const T* v, T* acc) {
+// acc += U^dag v, accumulated in place (no scaling).
+template <class T> __device__ __forceinline__ void adj_mat_vec_add(const T* u, const T* v, T* acc) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      acc[2 * i] = fma(-u[6 * k + 2 * i], v[2 * k], acc[2 * i]);
-      acc[2 * i] = fma(-u[6 * k + 2 * i + 1], v[2 * k + 1], acc[2 * i]);
-      acc[2 * i + 1] = fma(-u[6 * k + 2 * i], v[2 * k + 1], acc[2 * i + 1]);
-      acc[2 * i + 1] = fma(u[6 * k + 2 * i + 1], v[2 * k], acc[2 * i + 1]);
+      acc[2 * i] = fma(u[6 * k + 2 * i], v[2 * k], acc[2 * i]);
+      acc[2 * i] = fma(u[6 * k + 2 * i + 1], v[2 * k + 1], acc[2 * i]);
+      acc[2 * i + 1] = fma(u[6 * k + 2 * i], v[2 * k + 1], acc[2 * i + 1]);
+      acc[2 * i + 1] = fma(-u[6 * k + 2 * i + 1], v[2 * k], acc[2 * i + 1]);
     }
   }
 }
