@@ -153,8 +153,8 @@ __device__ __forceinline__ void wilson_direction(const WilsonKArgs& a, size_t rb
   half_project<MU, -SIGN>(p, h);
 #pragma unroll
   for (int k = 0; k < 12; ++k) g[k] = T(0);
-  mat_vec_acc(u, h, g, T(1));
-  mat_vec_acc(u, h + 6, g + 6, T(1));
+  mat_vec_add(u, h, g);
+  mat_vec_add(u, h + 6, g + 6);
   half_accumulate<MU, -SIGN>(g, acc);
   // backward: (1 + s gamma_mu) U_mu(x-mu)^dag in(x-mu); that link lives in block (mu, 1-out_par)
   L::load(a.gauge + (size_t)(2 * MU + 1 - a.out_par) * a.blk_bytes, a.G.S, cbb, u);
@@ -163,8 +163,8 @@ __device__ __forceinline__ void wilson_direction(const WilsonKArgs& a, size_t rb
   half_project<MU, SIGN>(p, h);
 #pragma unroll
   for (int k = 0; k < 12; ++k) g[k] = T(0);
-  adj_mat_vec_acc(u, h, g, T(1));
-  adj_mat_vec_acc(u, h + 6, g + 6, T(1));
+  adj_mat_vec_add(u, h, g);
+  adj_mat_vec_add(u, h + 6, g + 6);
   half_accumulate<MU, SIGN>(g, acc);
 }
 
