@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
     for (int k = 0; k < 18; ++k) a[k] = sA[threadIdx.x * 18 + k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) { v[k] = sb[threadIdx.x * 6 + k]; r[k] = 0; }
-    if (ADJ) adj_mat_vec_acc(a, v, r, T(1));
-    else mat_vec_acc(a, v, r, T(1));
+    if (ADJ) adj_mat_vec_add(a, v, r);
+    else mat_vec_add(a, v, r);
 #pragma unroll
     for (int k = 0; k < 6; ++k) sb[threadIdx.x * 6 + k] = r[k];
   }
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(kThreads) k_su3_hwvec(const T* __restrict__ A,
     for (int k = 0; k < 12; ++k) { v[k] = sh[threadIdx.x * 12 + k]; r[k] = 0; }
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
-      if (ADJ) adj_mat_vec_acc(a, v + 6 * sp, r + 6 * sp, T(1));
-      else mat_vec_acc(a, v + 6 * sp, r + 6 * sp, T(1));
+      if (ADJ) adj_mat_vec_add(a, v + 6 * sp, r + 6 * sp);
+      else mat_vec_add(a, v + 6 * sp, r + 6 * sp);
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) sh[threadIdx.x * 12 + k] = r[k];
