@@ -86,41 +86,30 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const char* __restrict_
     }
     T u[18];
     L::load(gauge + (size_t)(2 * mu + par) * blk_bytes, G.S, cb, u);
-    // Z_ij = s a_i conj(b_j)
-    C2<T> Z[3][3];
+    // With a' = 2 s a:  G = 2 Z^dag = b a'^dag  (G_ij = b_i conj(a'_j)), and
+    // A = U G^dag = U a' b^dag = (U a') b^dag:  the link product is a mat-vec followed by
+    // an outer product (su3_projector, Table 1), not a 3x3 matrix product.
+    T ap[6], w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      ap[k] = T(2) * s * a[k];
+      w[k] = T(0);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        C2<T> p = cmul_conj(C2<T>{a[2 * i], a[2 * i + 1]}, C2<T>{b[2 * j], b[2 * j + 1]});
-        Z[i][j] = {s * p.r, s * p.i};
+        const C2<T> q = cmul_conj(C2<T>{b[2 * i], b[2 * i + 1]}, C2<T>{ap[2 * j], ap[2 * j + 1]});
+        g[2 * (3 * i + j)] = q.r;
+        g[2 * (3 * i + j) + 1] = q.i;
       }
-    // G = 2 Z^dag: G_ij = 2 conj(Z_ji)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        g[2 * (3 * i + j)] = T(2) * Z[j][i].r;
-        g[2 * (3 * i + j) + 1] = -T(2) * Z[j][i].i;
-      }
+    mat_vec_add(u, ap, w);
     {
-      // A = U G^dag = 2 U Z
       C2<T> A[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          T re = 0, im = 0;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const T ur = u[2 * (3 * i + k)], ui = u[2 * (3 * i + k) + 1];
-            re = fma(ur, Z[k][j].r, re);
-            re = fma(-ui, Z[k][j].i, re);
-            im = fma(ur, Z[k][j].i, im);
-            im = fma(ui, Z[k][j].r, im);
-          }
-          A[i][j] = {T(2) * re, T(2) * im};
-        }
+        for (int j = 0; j < 3; ++j) A[i][j] = cmul_conj(C2<T>{w[2 * i], w[2 * i + 1]}, C2<T>{b[2 * j], b[2 * j + 1]});
       // TA(A) = (A - A^dag)/2 - Tr(A - A^dag)/6 * 1; Tr(A - A^dag) = 2i Im Tr A
       const T trim = (A[0][0].i + A[1][1].i + A[2][2].i) / T(3);
 #pragma unroll
