@@ -354,20 +354,21 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all"):
         del gauges, ins, ts, outs
         torch.cuda.empty_cache()
     if want("32c4"):
-        # FP32-18 at 32^4 (327 MB per copy: every launch reads its links from HBM)
+        # FP32 and BF16 at 32^4 (109-327 MB per copy: every launch reads its links from HBM)
         d4 = (32, 32, 32, 32)
         Vh4 = synth.volume(d4) // 2
         U4 = torch.from_numpy(synth.gauge_field(d4, "near_identity", seed=3, eps=0.3)).cuda()
-        for prec, recon in (("f32", 18), ("f32", 12)):
-            sb = site_bytes(prec, recon, "f32")
+        for prec, recon, vec in (("f32", 18, "f32"), ("f32", 12, "f32"), ("bf16", 18, "bf16"), ("bf16", 12, "bf16")):
+            sb = site_bytes(prec, recon, vec)
             K = ring_size(Vh4 * sb, l2, nstreams)
-            gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, "f32", K)
-            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
+            gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, vec, K)
+            vc = lq.PREC[vec]
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
             ms, launches, _ = time_steps(torch, g, 5, 3, stream)
             del g
             us = ms * 1000.0 / launches
             gbs = Vh4 * sb / us / 1e3
-            out[f"{prec}/{recon}/f32/32x32x32x32"] = {"gflops": round(Vh4 * FLOPS_PER_SITE / us / 1e3, 1),
+            out[f"{prec}/{recon}/{vec}/32x32x32x32"] = {"gflops": round(Vh4 * FLOPS_PER_SITE / us / 1e3, 1),
                                                       "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
                                                       "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
             del gauges, ins, ts, outs
