@@ -260,12 +260,16 @@ lq_status dslash_force(lq_context* ctx, const lq_gauge* U, double mass, const vo
 /* Batched solve of nlat independent lattices (uneven sizes allowed, at most 16), each with
  * nrhs right-hand sides and its own mass: every system (lattice, rhs) runs the cg_solve
  * iteration, but each phase of an iteration is ONE launch over all lattices -- a
- * persistent multi-lattice Dslash kernel walking (lattice, rhs tile, site block) tiles, and
+ * persistent multi-lattice Dslash kernel walking (lattice, rhs tile, site block) tiles
+ * (per thread, or spread over the warps of a block with the links shared), and
  * persistent vector kernels walking (lattice, rhs, site block) tiles -- and the iteration
  * block is captured once as a CUDA graph.  Tile shapes (sites per block, right-hand sides
  * per thread, threads per site) come from the autotuner, keyed by the lattice set.
  *   U_hi[l]: LQ_F64 gauges (all the same recon).  U_lo: NULL (FP64 solve) or an array of
- *   reduced-precision gauges of one format (mixed precision as in cg_solve).
+ *   reduced-precision gauges of one format (mixed precision as in cg_solve).  Reliable
+ *   updates are taken per lattice: when one system of a lattice is due, all of that
+ *   lattice's right-hand sides take it (as in cg_solve), and the FP64 work of the other
+ *   lattices is skipped.
  *   mass[l], b[l], x[l]: host arrays of nlat entries; b[l], x[l] are device complex128
  *   [nrhs][Vh_l][3].  stats: host array of nlat * nrhs entries, [l * nrhs + rhs].
  * Paper: the batching pattern is not in the paper; each system is the CG of cg_solve. */
