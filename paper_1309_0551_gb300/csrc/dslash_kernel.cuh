@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
     dslash_epilogue<VP, NR, TPS>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, a.reduce, a.rhs_stride, a.nrhs,
                                  rhs0, cb, sub, part);
   pdl_trigger();  // this block's main work is done: the successor may be scheduled
-  if (a.reduce != RED_NONE) block_reduce<NR>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
+  if (a.reduce != RED_NONE) block_reduce<NR, false>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 
 // Host side: launch one instance.  Supported (rhs tile, threads per site) pairs:

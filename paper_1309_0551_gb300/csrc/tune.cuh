@@ -162,7 +162,10 @@ __device__ __forceinline__ double warp_sum(double x) {
 // the grid to arrive sums them in column order (deterministic for a given launch shape)
 // and runs the finisher, except under FIN_DEFER, where a later launch sums them.  No
 // thread ever waits on another block.
-template <int NR>
+// kWideFinish: the last block sums each row with all its threads (short tail; for kernels
+// that finish every launch, like the CG update) or one warp per row (fewer registers for
+// the whole kernel: the compiler sizes it for this rarely run path too).
+template <int NR, bool kWideFinish = true>
 __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs,
                                              int bx, int nbx) {
   __shared__ double sm[NR][32];
@@ -194,18 +197,28 @@ __device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reduce
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // the whole block sums each row (strided by thread, then a fixed tree): deterministic
-  for (int rhs = 0; rhs < nrhs; ++rhs) {
-    double x = 0.0;
-    for (int b = threadIdx.x; b < nbx; b += blockDim.x) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
-    x = warp_sum(x);
-    __syncthreads();                       // sm[0][] free again
-    if (lane == 0) sm[0][warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      double y = lane < nw ? sm[0][lane] : 0.0;
-      y = warp_sum(y);
-      if (lane == 0) finish_one(red, rhs, y);
+  if constexpr (!kWideFinish) {
+    // one warp per row, lanes strided, then a fixed shuffle tree: deterministic
+    for (int rhs = warp; rhs < nrhs; rhs += nw) {
+      double x = 0.0;
+      for (int b = lane; b < nbx; b += 32) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
+      x = warp_sum(x);
+      if (lane == 0) finish_one(red, rhs, x);
+    }
+  } else {
+    // the whole block sums each row (strided by thread, then a fixed tree): deterministic
+    for (int rhs = 0; rhs < nrhs; ++rhs) {
+      double x = 0.0;
+      for (int b = threadIdx.x; b < nbx; b += blockDim.x) x += __ldcg(red.partials + (size_t)rhs * nbx + b);
+      x = warp_sum(x);
+      __syncthreads();                       // sm[0][] free again
+      if (lane == 0) sm[0][warp] = x;
+      __syncthreads();
+      if (warp == 0) {
+        double y = lane < nw ? sm[0][lane] : 0.0;
+        y = warp_sum(y);
+        if (lane == 0) finish_one(red, rhs, y);
+      }
     }
   }
   if (threadIdx.x == 0) *red.counter = 0u;
