@@ -45,7 +45,11 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
     dslash_epilogue<VP, NR, TPS>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, a.reduce, a.rhs_stride, a.nrhs,
                                  rhs0, cb, sub, part);
   pdl_trigger();  // this block's main work is done: the successor may be scheduled
-  if (a.reduce != RED_NONE) block_reduce<NR, false>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
+  // The compiler sizes and schedules the whole kernel with the finisher in it.  Measured:
+  // with 12-real links the whole-block finisher raised the plain operator from 48 to 58
+  // registers; with 18-real links the one-warp finisher slowed it (13.7 -> 17.4 us for a
+  // lone 16^3 x 32 FP32 launch).  Each format keeps the finisher it runs fastest with.
+  if (a.reduce != RED_NONE) block_reduce<NR, R == 18>(part, a.red, rhs0, a.nrhs, bx, gridDim.x / nty);
 }
 
 // Host side: launch one instance.  Supported (rhs tile, threads per site) pairs:
