@@ -45,6 +45,49 @@ def test_mixed_cg_reaches_fp64_tolerance(prec, recon):
     assert np.linalg.norm(sol - ref) / np.linalg.norm(ref) < 1e-10 * np.linalg.cond(M)
 
 
+def test_replaced_beta_hand_values():
+    # r_k = (1, 0, 0), ||r_k||^2 = 1.  Orthogonal new residual: the Fletcher-Reeves value.
+    rk = np.array([1.0, 0.0, 0.0], dtype=complex)
+    assert cg.replaced_beta(np.array([0.0, 2.0, 1j]), rk, 1.0) == 5.0
+    # r_new = (3, 4i, 0): Re<r_new, r_new - r_k> = 25 - 3 = 22
+    assert cg.replaced_beta(np.array([3.0, 4j, 0.0]), rk, 1.0) == 22.0
+    # r_new = (2, 0, 0) with ||r_k||^2 = 2: (4 - 2) / 2 = 1; r_new = r_k / 2: negative -> 0
+    assert cg.replaced_beta(np.array([2.0, 0, 0], dtype=complex), rk, 2.0) == 1.0
+    assert cg.replaced_beta(0.5 * rk, rk, 1.0) == 0.0
+
+
+def test_mixed_cg_with_exact_inner_is_plain_cg():
+    """With nothing rounded (FP64 links and vectors inside) the reliable updates replace the
+    residual by itself up to rounding: the iteration is the textbook CG, so it takes the
+    FP64 solver's iteration count (within the few extra iterations its checks cost) and
+    lands on the dense solution."""
+    dims, mass = (4, 4, 4, 4), 0.01
+    U = synth.gauge_field(dims, "haar", seed=4)
+    b = synth.fermion_field(dims, 1, 5)[0]
+    _, ref_info = cg.cg(U, b, mass, dims, tol=1e-10, maxiter=5000)
+    sol, info = cg.mixed_cg(U, b, mass, dims, tol=1e-10, prec="f64", recon=18, vec_prec="f64",
+                            maxiter=5000)
+    assert info["true_rel_resid"] <= 1e-10
+    assert abs(info["iters"] - ref_info["iters"]) <= 0.03 * ref_info["iters"]
+    M = dslash.dense_normal(U, mass, dims)
+    ref = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(sol - ref) / np.linalg.norm(ref) < 1e-10 * np.linalg.cond(M)
+
+
+def test_mixed_cg_bf16_links_haar_m001():
+    """BF16 links (8 significant bits) at m = 0.01 on Haar links, where the rounded operator
+    differs from the FP64 one by far more than m^2: the reliable updates with the
+    Polak-Ribiere beta still reach the FP64 true residual 1e-10."""
+    dims, mass = (4, 4, 4, 4), 0.01
+    U = synth.gauge_field(dims, "haar", seed=4)
+    b = synth.fermion_field(dims, 1, 5)[0]
+    sol, info = cg.mixed_cg(U, b, mass, dims, tol=1e-10, prec="bf16", recon=12, maxiter=12000)
+    assert info["true_rel_resid"] <= 1e-10
+    M = dslash.dense_normal(U, mass, dims)
+    ref = np.linalg.solve(M, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(sol - ref) / np.linalg.norm(ref) < 1e-10 * np.linalg.cond(M)
+
+
 # ---------------------------------------------------------------- gradients -----------
 
 DIMS, MASS = (4, 4, 4, 4), 0.3

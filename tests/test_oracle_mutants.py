@@ -1,8 +1,8 @@
 """The oracle's pins reject plausible mistakes: each test plants one in a copy of an oracle
 routine (on the CPU) and checks that a pin used elsewhere in the suite fails on it, while
 the unmodified routine passes.  Planted: a backward hop without the adjoint, a staggered
-phase taken from the wrong coordinate, the Wilson projectors swapped, and a TA projection
-that forgets the trace."""
+phase taken from the wrong coordinate, the Wilson projectors swapped, a TA projection
+that forgets the trace, and the Fletcher-Reeves beta after a reliable update."""
 import numpy as np
 
 import synth
@@ -76,3 +76,16 @@ def test_ta_without_trace_removal_is_caught():
         traceless = np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-13
         antiherm = np.abs(F + adj(F)).max() < 1e-13
         assert (traceless and antiherm) == ok
+
+
+def test_fletcher_reeves_beta_after_replacement_is_caught(monkeypatch):
+    """The mixed CG's pin at 4^4, BF16 links, m = 0.01 (1e-10 within 12000 iterations)
+    fails when the beta after a residual replacement is ||r_new||^2 / ||r_k||^2."""
+    from oracle import cg
+    dims, mass = (4, 4, 4, 4), 0.01
+    U = synth.gauge_field(dims, "haar", seed=4)
+    b = synth.fermion_field(dims, 1, 5)[0]
+    monkeypatch.setattr(cg, "replaced_beta",
+                        lambda r_new, r_k, rr_k: float(np.vdot(r_new, r_new).real) / rr_k)
+    _, info = cg.mixed_cg(U, b, mass, dims, tol=1e-10, prec="bf16", recon=12, maxiter=12000)
+    assert info["true_rel_resid"] > 1e-10
