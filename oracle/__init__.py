@@ -18,6 +18,9 @@ Modules
   improved   improved staggered Dslash (one-hop fat + three-hop Naik links), long-link builder
   md         molecular-dynamics link and momentum updates (exp, reunitarisation, leapfrog)
   wilson     Wilson hopping term (DeGrand-Rossi gammas) and its half-spinor form (Table 1 hwvec)
+  cxx        the FP64 C++ oracle (cpp/oracle.cpp: Dslash, M, CG, Table 1 products), plain loops
+             parallel over sites, timed on the host cores by bench.py; pinned by the same
+             brute-force, invariant and closed-form checks, and against this numpy code
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than itself
 (brute force, closed forms, invariants, finite differences); see ``tests/test_oracle_*.py``.
