@@ -37,15 +37,16 @@ APPS = 100                 # Dslash applications per step
 FLOPS_PER_SITE = 570
 BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
 # GB300's nominal FP64 rate, 1.25 TFLOP/s (about two FP64 FMAs per SM and clock: 152 SMs at
-# 2.07 GHz): the denominator of the FP64 kernels' ALU roofline.
-FP64_PEAK_GFLOPS = 1250.0
+# 2.07 GHz), for context; the FP64 kernels' ALU roofline divides by the rate measured on the
+# device itself (lq_fp64_fma_rate, independent FMA chains on every SM).
+FP64_NOMINAL_GFLOPS = 1250.0
 
-# DRAM bytes per k_dslash launch from the ncu capture summarised under profiles/ (key:
-# storage format), with the hash of the kernel sources it was taken on.  A changed kernel
-# makes the figure stale and the bench reports null.
+# DRAM bytes per k_dslash launch from an ncu capture of the same workload (key: storage
+# format), with the hash of the kernel sources it was taken on.  A changed kernel makes the
+# figure stale and the bench reports null.
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one k_dslash<f32,18,f32,1,1> launch
-    # (block 128, grid 512): 39,350,016 + 2,560 B (profiles/k_dslash_f32_18_16c32.md)
+    # (block 128, grid 512): 39,350,016 + 2,560 B
     "f32/18/f32/16x16x16x32/1": (39352576, "327c3035101626f6"),
 }
 KERNEL_SOURCES = ("paper_1309_0551_gb300/csrc/dslash_args.cuh",
@@ -306,7 +307,7 @@ def cpu_baseline(dims, seconds=12.0):
                       f"{'x'.join(map(str, dims))} lattice ({dt:.1f} s)"}
 
 
-def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all"):
+def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64_peak=FP64_NOMINAL_GFLOPS):
     """The per-format, operator and SU(3)-batch lines; `groups` (comma-separated, or "all")
     picks among formats, l2_warm, 32c4, improved, wilson, multi_rhs, su3."""
     import synth
@@ -498,6 +499,38 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all"):
                 out[f"su3_matvec/{prec}/adj{adj}"] = {"gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1),
                                                       "frac": round(gbs / peak, 3), "us": round(us, 2), "n": n}
             del As, bs, cs
+        # the same mat-vec with 12-real and 16-bit storage (su3_matvec_batch_ex)
+        for mat, recon, vec in (("f64", 12, "f64"), ("f32", 12, "f32"), ("bf16", 18, "bf16"),
+                                ("bf16", 12, "bf16"), ("f16", 12, "f16"), ("bf16", 12, "f32")):
+            per = n * (recon * BYTES[mat] + 12 * BYTES[vec])
+            K = ring_size(per, l2)
+            rows = A[:, :2, :].contiguous() if recon == 12 else A
+
+            def dev(z, prec):
+                if prec == "f64":
+                    return z.cuda()
+                if prec == "f32":
+                    return z.to(torch.complex64).cuda()
+                dt = torch.bfloat16 if prec == "bf16" else torch.float16
+                return torch.view_as_real(z).to(dt).contiguous().cuda()
+            As = [dev(rows, mat) for _ in range(K)]
+            bs = [dev(b, vec) for _ in range(K)]
+            cs = [torch.empty_like(bs[0]) for _ in range(K)]
+            for adj in (0, 1):
+                def step(ss, As=As, bs=bs, cs=cs, mat=mat, recon=recon, vec=vec, adj=adj):
+                    for i in range(20):
+                        lq.su3_matvec_batch_ex(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, mat, recon, vec, ss[0])
+                    return 20
+                g = GraphStep(torch, step, 1)
+                ms, launches, _ = time_steps(torch, g, 5, 2, stream)
+                del g
+                us = ms * 1000.0 / launches
+                gbs = per / us / 1e3
+                out[f"su3_matvec/{mat}/{recon}/{vec}/adj{adj}"] = {
+                    "gflops": round(n * 66 / us / 1e3, 1), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                    "us": round(us, 2), "n": n, "bytes_per_item": recon * BYTES[mat] + 12 * BYTES[vec]}
+            del As, bs, cs
+        ctx.sync()   # every bulk-copy wait of the batched kernels delivered (LQ_ERR_TIMEOUT otherwise)
         # mult_su3_nn / an / na over the 4V links (pairs of Haar matrices)
         B2 = torch.from_numpy(synth.haar_su3(synth.rng(11), n))
         for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
@@ -525,12 +558,12 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all"):
         g = GraphStep(torch, lambda ss: [lq.su3_mul_batch(ctx, Ad, Bd, Cd, 1024, 0, 0, None, ss[0]) for _ in range(20)] and 20, 1)
         ms, launches, _ = time_steps(torch, g, 5, 2, stream)
         out["su3_mul/f64/1024_pairs_us"] = round(ms * 1000.0 / launches, 2)
-    # FP64 kernels are bound by GB300's FP64 ALU, not by HBM: their roofline is the FP64
-    # peak (algorithmic flops, the same counts as "gflops")
+    # FP64 kernels are bound by GB300's FP64 ALU, not by HBM: their roofline is the measured
+    # FP64 FMA rate (algorithmic flops, the same counts as "gflops")
     for k, v in out.items():
         if isinstance(v, dict) and "/f64/" in f"/{k}/":
             v["bound"] = "fp64_alu"
-            v["alu_frac"] = round(v["gflops"] / FP64_PEAK_GFLOPS, 3)
+            v["alu_frac"] = round(v["gflops"] / fp64_peak, 3)
     return out
 
 
@@ -543,6 +576,7 @@ def run_cg(lq, ctx, torch, maxiter=20000):
     x = torch.empty_like(b)
     hi = lq.lq_gauge_pack(ctx, dims, U, "f64", 18)
     res = {"workload": "32^4 Haar SU(3), m=0.01, Gaussian source, tol 1e-10 (FP64 true residual)"}
+    x64 = None
     for name, prec, recon in (("fp64", None, 18), ("mixed_f32_12", "f32", 12), ("mixed_f16_12", "f16", 12),
                               ("mixed_bf16_12", "bf16", 12)):
         lo = lq.lq_gauge_pack(ctx, dims, U, prec, recon) if prec else None
@@ -561,6 +595,11 @@ def run_cg(lq, ctx, torch, maxiter=20000):
         dt = time.perf_counter() - t0
         res[name] = {"seconds": round(dt, 4), "iters": st["iters"], "reliable_updates": st["reliable_updates"],
                      "true_rel_resid": st["true_rel_resid"], "converged": ok}
+        if prec is None:
+            x64 = x.clone()
+        elif x64 is not None:
+            # error of the mixed solution against the FP64 solution of the same system
+            res[name]["x_rel_err_vs_fp64"] = float(torch.linalg.vector_norm(x - x64) / torch.linalg.vector_norm(x64))
     if res["fp64"]["converged"]:
         for k in ("mixed_f32_12", "mixed_f16_12", "mixed_bf16_12"):
             if res[k]["converged"]:
@@ -704,9 +743,13 @@ def run_ours(args):
 
     extra = {}
     if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
+        fp64 = ctx.fp64_fma_rate()
+        extra["fp64_peak"] = {"gflops": round(fp64, 1), "nominal_gflops": FP64_NOMINAL_GFLOPS,
+                              "source": "measured: lq_fp64_fma_rate (8 independent FMA chains per thread, "
+                                        "every SM, CUDA events, best of 3)"}
         U_var = U_dev if dims == DIMS else torch.from_numpy(
             synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)).cuda()
-        extra["variants"] = run_variants(lq, ctx, torch, U_var, l2, stream, args.streams, args.variants)
+        extra["variants"] = run_variants(lq, ctx, torch, U_var, l2, stream, args.streams, args.variants, fp64)
     if rank == 0 and not args.no_cg:
         ctx.set_tuning(1)  # the solvers issue one launch at a time
         extra["cg"] = run_cg(lq, ctx, torch, args.cg_maxiter)

@@ -75,6 +75,28 @@ lq_status lq_destroy(lq_context* ctx);
 const char* lq_last_error(const lq_context* ctx);
 /* Name of a status code. */
 const char* lq_status_string(lq_status s);
+/* Synchronise `stream`, then report and clear the context's device status word: the
+ * flags that bounded device waits set when they gave up since the last lq_sync.  Such a
+ * wait exists in the batched SU(3) kernels (su3_*_batch), where one thread per block
+ * waits, at most ~2^24 polls, for the TMA bulk copies that bring the block's operand slice
+ * into shared memory; if they do not arrive, the block records the failure, waits once
+ * more (bounded) so that it does not leave with copies in flight, and skips its work.
+ * Those entry points are asynchronous and return LQ_OK at launch, so their outputs can
+ * only be trusted after an lq_sync that returns LQ_OK.
+ * Returns LQ_ERR_TIMEOUT if any wait gave up (outputs of the calls issued on this context
+ * since the last lq_sync may be unwritten), LQ_ERR_CUDA for an error of the stream, LQ_OK
+ * otherwise. */
+lq_status lq_sync(lq_context* ctx, lq_stream stream);
+/* Diagnostics for the error path above: synchronise `stream` and OR `flags` into the
+ * context's device status word from the host, exactly as a device wait that gave up
+ * would; the next lq_sync reports LQ_ERR_TIMEOUT.  No kernel runs. */
+lq_status lq_inject_status(lq_context* ctx, unsigned int flags, lq_stream stream);
+/* Self-test of the bounded device wait: one block of the batched mat-vec kernel arms its
+ * mbarrier for its operand bytes but issues no copy, so its (short, ~2^10 polls) wait runs
+ * out with nothing in flight; the block sets the status flag and returns.  The next
+ * lq_sync returns LQ_ERR_TIMEOUT.  Asynchronous on `stream`. */
+lq_status lq_selftest_wait_timeout(lq_context* ctx, lq_stream stream);
+
 /* Autotuning of launch shapes (threads per block, right-hand sides per thread, threads per
  * site).  mode 0: off, fixed defaults.  mode 1 (the default, unless the environment sets
  * LQCD_TUNE=0): each new shape key is tuned on its first call by timing every candidate
@@ -89,6 +111,14 @@ lq_status lq_set_tuning(lq_context* ctx, int mode);
 /* Write the tuning table (one line per key: key, chosen block, rhs tile, microseconds)
  * into buf (NUL-terminated, truncated to len).  *needed receives the full length + 1. */
 lq_status lq_tune_report(const lq_context* ctx, char* buf, size_t len, size_t* needed);
+
+/* Measure the device's FP64 FMA rate (GFLOP/s, 2 flops per FMA) with a kernel of
+ * independent FMA chains on every SM, timed with CUDA events (best of three after a
+ * warm-up run; synchronises the device's legacy stream).  GB300 runs FP64 far below its
+ * FP32 rate: the FP64 kernels here are bound by this pipe, and this figure is the
+ * denominator of their roofline.  The paper has no counterpart (its peak figure is the
+ * Pentium 4's, Sec. 2). */
+lq_status lq_fp64_fma_rate(lq_context* ctx, double* gflops);
 
 /* ------------------------------------------------------------------- gauge ---------- */
 
@@ -122,6 +152,20 @@ lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B, void* C, 
  * A: device complex [n][3][3]; b, c: device complex [n][3]; prec LQ_F64 or LQ_F32. */
 lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void* b, void* c,
                            int64_t n, int adj, lq_prec prec, lq_stream stream);
+
+/* su3_matvec_batch with any storage format: c[i] = op(A[i]) b[i] (Table 1:
+ * mult_su3_mat_vec, adj 0, and mult_adj_su3_mat_vec, adj 1, whose first component is
+ * Eqs. (1.1)-(2.3)); 66 flops each.
+ *   A: device, complex [n][3][3] of mat_prec with recon LQ_RECON_18, or complex [n][2][3]
+ *      (rows 0 and 1 only) with LQ_RECON_12: row 2 is rebuilt as conj(row0 x row1), exact
+ *      for SU(3) matrices up to rounding.  16-bit complex values are (re, im) pairs of
+ *      bfloat16 / binary16 (4 bytes per complex).
+ *   b, c: device complex [n][3] of vec_prec; c must not overlap A or b.
+ *   Pairs: LQ_F64 matrices with LQ_F64 vectors (FP64 arithmetic); LQ_F32 / LQ_BF16 /
+ *   LQ_F16 matrices with LQ_F32 / LQ_BF16 / LQ_F16 vectors (FP32 arithmetic, one rounding
+ *   of each output real).  n = 0 is a no-op. */
+lq_status su3_matvec_batch_ex(lq_context* ctx, const void* A, const void* b, void* c, int64_t n, int adj,
+                              lq_prec mat_prec, lq_recon recon, lq_prec vec_prec, lq_stream stream);
 
 /* c[i] = op(A[i]) h[i] for half Wilson vectors h (two colour vectors, i.e. two spin
  * components); op = adjoint when adj = 1.  Table 1: mult_su3_mat_hwvec (adj 0) and
@@ -229,6 +273,12 @@ typedef struct {
  *         FP32 with FP64 inner products, and replaces its residual by the FP64 true
  *         residual (reliable update) every params->reliable_every iterations, or when it
  *         fell below params->delta times the last replaced one, or on apparent convergence.
+ *         The search direction is kept across a replacement, with the Polak-Ribiere
+ *         beta = max(0, Re<r_new, r_new - r_k>) / ||r_k||^2 (r_k: the residual that
+ *         entered the last iteration; equal to ||r_new||^2 / ||r_k||^2 in exact
+ *         arithmetic), the choice of flexible CG for an operator that differs from the
+ *         one the residual is corrected with.  The FP64 solve restarts the same way when
+ *         its iterated residual meets tol but its true residual does not.
  *   b, x: device complex128 [nrhs][Vh][3]; x is overwritten.  nrhs in [1, 16].
  *   stats: host array of nrhs entries (may be NULL).
  * Synchronises `stream` at each check (every check_every iterations).  Returns
@@ -291,7 +341,7 @@ lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge* const* U_h
  *   at each check.  Launch shapes come from the context's tuning table when an earlier
  *   call (e.g. cg_solve with the same gauges) filled it, else fixed defaults.
  *   Limit: (4 inner vectors, 5 with U_lo) * nrhs * Vh * 48 bytes (24 with U_lo) + 2 FP64
- *   vectors of nrhs * Vh * 48 bytes + nrhs * Vh/16 * 8 bytes of partials must fit in
+ *   vectors of nrhs * Vh * 48 bytes + 3 * nrhs * Vh/16 * 8 bytes of partials must fit in
  *   32 MiB (e.g. a 16^4 lattice with one right-hand side); larger problems get
  *   LQ_ERR_INVALID_ARG with a message naming the sizes.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)

@@ -62,6 +62,10 @@ def load(path: str | None = None):
         "lq_last_error": ([P], ctypes.c_char_p),
         "lq_status_string": ([I], ctypes.c_char_p),
         "lq_set_tuning": ([P, I], I),
+        "lq_fp64_fma_rate": ([P, ctypes.POINTER(D)], I),
+        "lq_sync": ([P, P], I),
+        "lq_inject_status": ([P, ctypes.c_uint, P], I),
+        "lq_selftest_wait_timeout": ([P, P], I),
         "lq_tune_report": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
         "lq_gauge_pack": ([P, ctypes.POINTER(I), P, I, I, ctypes.POINTER(P), P], I),
         "lq_gauge_free": ([P, P], I),
@@ -69,6 +73,7 @@ def load(path: str | None = None):
                            ctypes.POINTER(ctypes.c_size_t)], I),
         "su3_mul_batch": ([P, P, P, P, L, I, I, I, P], I),
         "su3_matvec_batch": ([P, P, P, P, L, I, I, P], I),
+        "su3_matvec_batch_ex": ([P, P, P, P, L, I, I, I, I, P], I),
         "dslash_eo": ([P, P, P, P, I, I, I, P], I),
         "cg_solve": ([P, P, P, D, P, P, I, ctypes.POINTER(lq_cg_params),
                       ctypes.POINTER(lq_cg_stats), P], I),
@@ -138,6 +143,25 @@ class Context:
     def set_tuning(self, mode):
         """0/False: off; 1/True: shapes for lone launches; 2: for concurrent launches."""
         self.check(self.lib.lq_set_tuning(self.handle, int(mode)))
+
+    def sync(self, stream=None):
+        """lq_sync: synchronise the stream and raise LQError (LQ_ERR_TIMEOUT) if a bounded
+        device wait gave up since the last sync."""
+        self.check(self.lib.lq_sync(self.handle, _stream(stream)))
+
+    def inject_status(self, flags: int, stream=None):
+        """lq_inject_status: set device status flags from the host (error-path tests)."""
+        self.check(self.lib.lq_inject_status(self.handle, int(flags), _stream(stream)))
+
+    def selftest_wait_timeout(self, stream=None):
+        """lq_selftest_wait_timeout: a bounded TMA wait that runs out with nothing in flight."""
+        self.check(self.lib.lq_selftest_wait_timeout(self.handle, _stream(stream)))
+
+    def fp64_fma_rate(self) -> float:
+        """lq_fp64_fma_rate: measured FP64 FMA rate of the device in GFLOP/s."""
+        g = ctypes.c_double()
+        self.check(self.lib.lq_fp64_fma_rate(self.handle, ctypes.byref(g)))
+        return g.value
 
     def tune_report(self) -> str:
         need = ctypes.c_size_t()
@@ -263,6 +287,16 @@ def su3_matvec_batch(ctx: Context, A, b, c, n=None, adj=0, prec=None, stream=Non
     prec = vec_prec_of(A) if prec is None else prec
     ctx.check(ctx.lib.su3_matvec_batch(ctx.handle, _ptr(A), _ptr(b), _ptr(c), int(n), int(adj),
                                        int(prec), _stream(stream)))
+
+
+def su3_matvec_batch_ex(ctx: Context, A, b, c, n, adj=0, mat_prec=LQ_F32, recon=18, vec_prec=None,
+                        stream=None):
+    """c[i] = op(A[i]) b[i] with matrices of ``mat_prec`` and ``recon`` reals (12: rows 0 and
+    1 stored, [n][2][3]) and vectors of ``vec_prec`` (default: the matrices' precision)."""
+    mat_prec = PREC[mat_prec] if isinstance(mat_prec, str) else int(mat_prec)
+    vec_prec = mat_prec if vec_prec is None else (PREC[vec_prec] if isinstance(vec_prec, str) else int(vec_prec))
+    ctx.check(ctx.lib.su3_matvec_batch_ex(ctx.handle, _ptr(A), _ptr(b), _ptr(c), int(n), int(adj), mat_prec,
+                                          int(recon), vec_prec, _stream(stream)))
 
 
 def su3_mat_hwvec_batch(ctx: Context, A, h, c, n=None, adj=0, prec=None, stream=None):

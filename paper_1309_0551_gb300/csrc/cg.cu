@@ -13,7 +13,13 @@
 //
 // Reliable update (mixed precision, and the FP64 solver's restart on apparent
 // convergence): x_hi += x_lo, r_hi = b - M_fp64 x_hi (two FP64 half Dslash, the second with
-// a fused ||r_hi||^2), r_lo = r_hi rounded, x_lo = 0, p kept, beta = ||r_lo||^2 / rr_prev.
+// a fused ||r_hi||^2), r_lo = r_hi rounded, x_lo = 0, p kept, and beta in the Polak-Ribiere
+// form max(0, Re<r_lo, r_lo - r_k>) / ||r_k||^2, r_k the residual that entered the last
+// iteration (rebuilt as r + alpha Ap).  Between replacements <r_{k+1}, r_k> vanishes up to
+// rounding and this is ||r_{k+1}||^2 / ||r_k||^2; at a replacement the corrected residual
+// is not the iterated one, and the Fletcher-Reeves form would carry a direction built with
+// the rounded operator into it: with BF16 links on Haar links at m = 0.01 that form
+// stalls near 1e-4, this one reaches 1e-10 (flexible CG: Golub & Ye 1999, Notay 2000).
 #include <math.h>
 #include <string.h>
 
@@ -71,13 +77,13 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, int cols, 
     CGScalars* s = sc + rhs;
     s->pAp = pAp;
     s->alpha = (s->active && pAp > 0.0) ? s->rr / pAp : 0.0;
+    if (s->active) s->alpha_last = s->alpha;
   }
   pdl_trigger();
 }
 
 // x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), grid-stride over
-// the rhs's 16-byte chunks.  The chunk's squares are summed in the vector precision, the
-// running sum in FP64.  (A TMA-tiled variant -- four bulk loads into shared memory, two
+// the rhs's 16-byte chunks.  The squares are summed in FP64.  (A TMA-tiled variant -- four bulk loads into shared memory, two
 // bulk stores -- measured slower than the grid-stride form: 21.8 vs 20.1 us FP32, 44 vs
 // 35 us FP64 at 32^4, with the per-site 8-byte accesses the grid-stride form then used.)
 template <lq_prec VP>
@@ -102,16 +108,14 @@ __global__ void __launch_bounds__(kBlas) k_cg_update(void* x, void* r, const voi
     C::get(rc[i], rv);
     C::get(__ldg(pc + i), pv);
     C::get(__ldg(ac + i), av);
-    T s = 0;
 #pragma unroll
     for (int k = 0; k < C::n; ++k) {
       xv[k] = fma(alpha, pv[k], xv[k]);
       rv[k] = fma(-alpha, av[k], rv[k]);
-      s = fma(rv[k], rv[k], s);
+      acc[0] = fma((double)rv[k], (double)rv[k], acc[0]);
     }
     xc[i] = C::put(xv);
     rc[i] = C::put(rv);
-    acc[0] += (double)s;
   }
   pdl_trigger();
   block_reduce<1>(acc, red, rhs, gridDim.y);
@@ -166,6 +170,40 @@ __global__ void __launch_bounds__(kBlas) k_convert(const void* src, void* dst, i
     }
   }
   if (reduce) block_reduce<1>(acc, red, rhs, gridDim.y);
+}
+
+// Residual replacement: r = round(r_hi) for every rhs, with two FP64 sums per rhs into
+// the FIN_STORE rows 2 rhs and 2 rhs + 1: ||r_new||^2 and, when `with_dot`,
+// Re<r_new, r_k> with r_k = r_old + alpha_last Ap rebuilt from the iterated residual r_old
+// this launch overwrites (the Polak-Ribiere beta of the replacement).
+template <lq_prec VL>
+__global__ void __launch_bounds__(kBlas) k_cg_replace(const double* rhi, void* r, const void* Ap, const CGScalars* sc,
+                                                      int Vh, int with_dot, Reducer red) {
+  using L = VecT<VL>;
+  using T = typename L::real;
+  const int rhs = blockIdx.y;
+  const size_t off = (size_t)rhs * Vh;
+  const T alpha = with_dot ? (T)sc[rhs].alpha_last : T(0);
+  double acc[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+    double h[6];
+    T n[6];
+    VecT<LQ_F64>::load(rhi, off + i, h);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      n[k] = (T)h[k];
+      acc[0] = fma((double)n[k], (double)n[k], acc[0]);
+    }
+    if (with_dot) {
+      T o[6], a[6];
+      L::load_rw(r, off + i, o);
+      L::load(Ap, off + i, a);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[1] = fma((double)n[k], (double)fma(alpha, a[k], o[k]), acc[1]);
+    }
+    L::store(r, off + i, n);
+  }
+  block_reduce<2>(acc, red, 2 * rhs, 2 * gridDim.y, blockIdx.x, gridDim.x);
 }
 
 // x_hi += x_lo; x_lo = 0.
@@ -302,6 +340,40 @@ __global__ void __launch_bounds__(kBlas) k_seg_convert(const void* src, void* ds
     block_sum_store<1>(acc, red.partials + (size_t)q * g.pstride + chunk, g.pstride, 1);
   }
   grid_finish(red, g.nlat * g.nrhs, g.pstride, [&](int q) { return g.lat[q / g.nrhs].tps; });
+}
+
+// Batched residual replacement of the systems whose ru flag is set: r = round(r_hi), with
+// ||r_new||^2 and Re<r_new, r_old + alpha_last Ap> into FIN_STORE rows 2q and 2q + 1
+// (zeros for the other systems); see k_cg_replace.
+template <lq_prec VL>
+__global__ void __launch_bounds__(kBlas) k_seg_replace(const double* rhi, void* r, const void* Ap, const SegArgs g,
+                                                       Reducer red, const CGScalars* sc) {
+  using L = VecT<VL>;
+  using T = typename L::real;
+  for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int q, chunk, Vh, l;
+    size_t base;
+    seg_locate(g, tile, q, base, chunk, Vh, l);
+    const int i = chunk * kBlas + threadIdx.x;
+    double acc[2] = {0.0, 0.0};
+    if (i < Vh && sc[q].ru) {
+      const T alpha = (T)sc[q].alpha_last;
+      double h[6];
+      T n[6], o[6], a[6];
+      VecT<LQ_F64>::load(rhi, base + i, h);
+      L::load_rw(r, base + i, o);
+      L::load(Ap, base + i, a);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        n[k] = (T)h[k];
+        acc[0] = fma((double)n[k], (double)n[k], acc[0]);
+        acc[1] = fma((double)n[k], (double)fma(alpha, a[k], o[k]), acc[1]);
+      }
+      L::store(r, base + i, n);
+    }
+    block_sum_store<2>(acc, red.partials + (size_t)(2 * q) * g.pstride + chunk, g.pstride, 2);
+  }
+  grid_finish(red, 2 * g.nlat * g.nrhs, g.pstride, [&](int q2) { return g.lat[(q2 / 2) / g.nrhs].tps; });
 }
 
 template <lq_prec VL>
@@ -574,22 +646,23 @@ lq_status fold_x(Solver& S) {
   return LQ_OK;
 }
 
-// r_lo = round(r_hi) with ||r_lo||^2 -> result; batched with `masked`: only the systems
-// whose ru flag is set.
-lq_status replace_residual(Solver& S, bool masked = false) {
+// r_lo = round(r_hi) with ||r_lo||^2 -> result[2 i] and, when `with_dot` (a replacement
+// during the iteration), Re<r_lo, r_k> -> result[2 i + 1] for the Polak-Ribiere beta.
+// Batched: only the systems whose ru flag is set (always with the dot).
+lq_status replace_residual(Solver& S, bool with_dot) {
   Reducer red = S.reducer(FIN_STORE);
   if (S.batch) {
     const Batch& B = *S.batch;
-    const CGScalars* mask = masked ? S.sc : nullptr;
-    if (S.mixed) k_seg_convert<LQ_F64, LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red, mask);
-    else k_seg_convert<LQ_F64, LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, B.seg, red, mask);
-    LQ_CHECK_LAUNCH(S.ctx, "k_seg_convert");
+    if (S.mixed) k_seg_replace<LQ_F32><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, B.seg, red, S.sc);
+    else k_seg_replace<LQ_F64><<<B.seg_grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, B.seg, red, S.sc);
+    LQ_CHECK_LAUNCH(S.ctx, "k_seg_replace");
     return LQ_OK;
   }
   dim3 grid(S.nbx, S.nrhs);
-  if (S.mixed) k_convert<LQ_F64, LQ_F32><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Vh, 1, red);
-  else k_convert<LQ_F64, LQ_F64><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Vh, 1, red);
-  LQ_CHECK_LAUNCH(S.ctx, "k_convert");
+  const CGScalars* sc = S.sc;
+  if (S.mixed) k_cg_replace<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, sc, S.Vh, with_dot ? 1 : 0, red);
+  else k_cg_replace<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, sc, S.Vh, with_dot ? 1 : 0, red);
+  LQ_CHECK_LAUNCH(S.ctx, "k_cg_replace");
   return LQ_OK;
 }
 
@@ -618,9 +691,11 @@ lq_status push_scalars(Solver& S) {
   return LQ_OK;
 }
 
-lq_status read_result(Solver& S, std::vector<double>& out) {
-  out.resize(S.nsys);
-  LQ_CUDA(S.ctx, cudaMemcpyAsync(out.data(), S.result, sizeof(double) * S.nsys, cudaMemcpyDeviceToHost, S.s));
+// The first `rows` (default: one per system) FIN_STORE totals.
+lq_status read_result(Solver& S, std::vector<double>& out, int rows = 0) {
+  const int n = rows ? rows : S.nsys;
+  out.resize(n);
+  LQ_CUDA(S.ctx, cudaMemcpyAsync(out.data(), S.result, sizeof(double) * n, cudaMemcpyDeviceToHost, S.s));
   LQ_CUDA(S.ctx, cudaStreamSynchronize(S.s));
   return LQ_OK;
 }
@@ -679,14 +754,21 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     bb[i] = res[i];
     if (!isfinite(bb[i])) return lq_fail(ctx, LQ_ERR_NUMERIC, "source %d holds NaN/Inf", i);
   }
-  st = replace_residual(S);
+  // r = round(b) for every system (the batched kernel replaces the systems flagged ru)
+  for (int i = 0; i < n; ++i) {
+    memset(&S.sc_host[i], 0, sizeof(CGScalars));
+    S.sc_host[i].ru = 1;
+  }
+  st = push_scalars(S);
   if (st) return st;
-  st = read_result(S, res);
+  st = replace_residual(S, /*with_dot=*/false);
+  if (st) return st;
+  st = read_result(S, res, 2 * n);
   if (st) return st;
   for (int i = 0; i < n; ++i) {
     CGScalars& c = S.sc_host[i];
     memset(&c, 0, sizeof c);
-    c.rr = res[i];
+    c.rr = res[2 * i];
     c.bb = bb[i];
     c.tol2 = tol2 * bb[i];
     c.rhi2 = bb[i];
@@ -775,10 +857,10 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
     std::vector<double> rhi2;
     st = read_result(S, rhi2);
     if (st) return st;
-    st = replace_residual(S, /*masked=*/S.batch != nullptr);
+    st = replace_residual(S, /*with_dot=*/true);
     if (st) return st;
-    std::vector<double> rlo2;
-    st = read_result(S, rlo2);
+    std::vector<double> rlo;   // [2 i]: ||r_lo||^2, [2 i + 1]: Re<r_lo, r_k>
+    st = read_result(S, rlo, 2 * n);
     if (st) return st;
     bool restarted = false;
     for (int i = 0; i < n; ++i) {
@@ -798,8 +880,9 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
       }
       if (!c.active) restarted = true;
       c.rhi2 = rhi2[i];
-      c.beta = c.rr_prev > 0.0 ? rlo2[i] / c.rr_prev : 0.0;
-      c.rr = rlo2[i];
+      const double pr = c.rr_prev > 0.0 ? (rlo[2 * i] - rlo[2 * i + 1]) / c.rr_prev : 0.0;
+      c.beta = pr > 0.0 ? pr : 0.0;
+      c.rr = rlo[2 * i];
       c.active = 1;
     }
     if (restarted && !S.mixed && --restarts_left < 0) break;
@@ -878,8 +961,8 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
-  const size_t need = 5 * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +
-                      2 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
+  const size_t need = 5 * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 16) + 8 +
+                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
   void* base = nullptr;
   lq_status st = lq_scratch(ctx, need, &base);
   if (st) return st;
@@ -892,9 +975,9 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.rhi = (double*)A.take(v64);
   S.thi = (double*)A.take(v64);
   S.sc = (CGScalars*)A.take(sizeof(CGScalars) * nrhs);
-  S.result = (double*)A.take(sizeof(double) * nrhs);
+  S.result = (double*)A.take(sizeof(double) * 2 * nrhs);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
-  S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.partials = (double*)A.take(sizeof(double) * 2 * nrhs * S.nblocks_max);
   S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   st = host_scalars(ctx, nrhs);
@@ -998,8 +1081,8 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
-  const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 8) + 8 +
-                      2 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
+  const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 16) + 8 +
+                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
   if (need > kNoAllocScratchBytes)
     return lq_fail(ctx, LQ_ERR_INVALID_ARG,
                    "cg_solve_noalloc: %d right-hand sides on %d sites per parity need %zu bytes of scratch, "
@@ -1016,9 +1099,9 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.rhi = (double*)A.take(v64);
   S.thi = (double*)A.take(v64);
   S.sc = (CGScalars*)A.take(sizeof(CGScalars) * nrhs);
-  S.result = (double*)A.take(sizeof(double) * nrhs);
+  S.result = (double*)A.take(sizeof(double) * 2 * nrhs);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
-  S.partials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.partials = (double*)A.take(sizeof(double) * 2 * nrhs * S.nblocks_max);
   S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
   if (A.off > kNoAllocScratchBytes) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   CGScalars host_scalars[16];  // pageable host copy of the per-rhs scalars
@@ -1131,8 +1214,8 @@ extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge*
   B.seg_grid = tiles < 8 * ctx->num_sms ? tiles : 8 * ctx->num_sms;
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
-  const size_t need = 5 * vin + 4 * v64 + S.nsys * (sizeof(CGScalars) + 8) + 8 +
-                      (size_t)S.nsys * S.nblocks_max * sizeof(double) + 14 * 256;
+  const size_t need = 5 * vin + 4 * v64 + S.nsys * (sizeof(CGScalars) + 16) + 8 +
+                      2 * (size_t)S.nsys * S.nblocks_max * sizeof(double) + 14 * 256;
   void* base = nullptr;
   lq_status st = lq_scratch(ctx, need, &base);
   if (st) return st;
@@ -1147,9 +1230,9 @@ extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge*
   S.rhi = (double*)A.take(v64);
   S.thi = (double*)A.take(v64);
   S.sc = (CGScalars*)A.take(sizeof(CGScalars) * S.nsys);
-  S.result = (double*)A.take(sizeof(double) * S.nsys);
+  S.result = (double*)A.take(sizeof(double) * 2 * S.nsys);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
-  S.partials = (double*)A.take(sizeof(double) * S.nsys * S.nblocks_max);
+  S.partials = (double*)A.take(sizeof(double) * 2 * S.nsys * S.nblocks_max);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   st = host_scalars(ctx, S.nsys);
   if (st) return st;

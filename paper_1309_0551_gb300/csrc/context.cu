@@ -61,6 +61,12 @@ extern "C" lq_status lq_create(lq_context** out, int device) {
   if (e != cudaSuccess) { delete ctx; return LQ_ERR_CUDA; }
   ctx->num_sms = prop.multiProcessorCount;
   ctx->l2_bytes = prop.l2CacheSize;
+  if (cudaMalloc(&ctx->dev_status, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(ctx->dev_status, 0, sizeof(unsigned int)) != cudaSuccess) {
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
+    delete ctx;
+    return LQ_ERR_CUDA;
+  }
   const char* env = getenv("LQCD_TUNE");
   ctx->tuning = !(env && env[0] == '0');
   // "block,rhs_tile,threads_per_site", e.g. "128,1,2": every Dslash launch whose right-hand
@@ -86,8 +92,36 @@ extern "C" lq_status lq_destroy(lq_context* ctx) {
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->flush) cudaFree(ctx->flush);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
   }
   delete ctx;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_sync(lq_context* ctx, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  LQ_CUDA(ctx, cudaStreamSynchronize(s));
+  unsigned int flags = 0;
+  LQ_CUDA(ctx, cudaMemcpy(&flags, ctx->dev_status, sizeof flags, cudaMemcpyDeviceToHost));
+  if (!flags) return LQ_OK;
+  LQ_CUDA(ctx, cudaMemset(ctx->dev_status, 0, sizeof(unsigned int)));
+  return lq_fail(ctx, LQ_ERR_TIMEOUT,
+                 "a bounded device wait gave up (status flags 0x%x%s): the blocks that waited skipped their "
+                 "work, so outputs of the calls issued since the last lq_sync may be unwritten",
+                 flags, (flags & kDevTmaTimeout) ? ": TMA bulk copy not delivered" : "");
+}
+
+extern "C" lq_status lq_inject_status(lq_context* ctx, unsigned int flags, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int cur = 0;
+  LQ_CUDA(ctx, cudaStreamSynchronize(s));
+  LQ_CUDA(ctx, cudaMemcpy(&cur, ctx->dev_status, sizeof cur, cudaMemcpyDeviceToHost));
+  cur |= flags;
+  LQ_CUDA(ctx, cudaMemcpy(ctx->dev_status, &cur, sizeof cur, cudaMemcpyHostToDevice));
   return LQ_OK;
 }
 

@@ -26,8 +26,13 @@ struct TuneEntry {
 // blocks of 32 sites x rhs_tile warps, links shared through shared memory (k_dslash_rw).
 constexpr int kTpsRhsWarps = 8;
 
+// Flags of the context's device status word (lq_context::dev_status), set by kernels
+// whose bounded waits gave up; lq_sync reports and clears them.
+constexpr unsigned int kDevTmaTimeout = 1u;   // a TMA bulk copy did not arrive in time
+
 struct lq_context {
   int device = 0;
+  unsigned int* dev_status = nullptr;  // device word of kDev* flags (zero: no failure)
   int num_sms = 0;
   size_t l2_bytes = 0;
   std::string last_error;

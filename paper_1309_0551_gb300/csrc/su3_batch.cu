@@ -9,16 +9,17 @@
 // result slice leaves by a TMA bulk store.  Every byte of global memory is touched once,
 // in full sectors.  Slices whose size is not a multiple of 16 bytes (a ragged last block)
 // use coalesced 16-byte loads and stores by all threads instead.
+#include <type_traits>
+
 #include "lqcd_internal.cuh"
 #include "tma.cuh"
 #include "tune.cuh"
 
-// Blocks that gave up waiting for a bulk copy (should stay 0; see tma.cuh).
-__device__ unsigned int g_su3_tma_timeouts;
-
 namespace {
 
 constexpr int kThreads = 128;
+// Poll limit of the self-test instantiation (PROBE): its wait is meant to run out.
+constexpr long kProbeSpins = 1L << 10;
 
 // Copy `nreal` reals between global and shared memory with 16-byte accesses (both bases
 // 16-byte aligned) and a scalar tail.
@@ -45,20 +46,31 @@ __device__ __forceinline__ void copy_s2g(T* __restrict__ dst, const T* __restric
 __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // Brings nA reals from gA and nB from gB into shared memory (sA, sB); returns false if the
-// block must skip its work (a bulk copy did not arrive within the wait limit).  Ends with
-// a barrier.
-template <class T>
-__device__ __forceinline__ bool stage_in(T* sA, const T* gA, int nA, T* sB, const T* gB, int nB, uint64_t* bar) {
+// block must skip its work: the bulk copies did not arrive within the wait limit.  Then
+// kDevTmaTimeout is set in *status, and the thread waits once more (bounded) so that the
+// block does not leave while its copies may still be landing in its shared memory.  Ends
+// with a barrier.
+// PROBE (self-test only, lq_selftest_wait_timeout): the barrier is armed for the bytes but
+// no copy is issued and the limit is short, so the wait runs out with nothing in flight.
+template <bool PROBE = false, class T>
+__device__ __forceinline__ bool stage_in(T* sA, const T* gA, int nA, T* sB, const T* gB, int nB, uint64_t* bar,
+                                         unsigned int* status) {
   __shared__ int ok;
   const uint32_t bA = nA * sizeof(T), bB = nB * sizeof(T);
   if (bA % 16 == 0 && bB % 16 == 0 && aligned16(gA) && aligned16(gB)) {
     if (threadIdx.x == 0) {
+      const long limit = PROBE ? kProbeSpins : tma::kMbarSpinLimit;
       tma::mbar_init(bar, 1);
       tma::mbar_expect_tx(bar, bA + bB);
-      tma::load(sA, gA, bA, bar);
-      tma::load(sB, gB, bB, bar);
-      ok = tma::mbar_wait(bar, 0);
-      if (!ok) atomicAdd(&g_su3_tma_timeouts, 1u);
+      if (!PROBE) {
+        tma::load(sA, gA, bA, bar);
+        tma::load(sB, gB, bB, bar);
+      }
+      ok = tma::mbar_wait(bar, 0, limit);
+      if (!ok) {
+        atomicOr(status, kDevTmaTimeout);
+        if (!PROBE) tma::mbar_wait(bar, 0, limit);
+      }
     }
     __syncthreads();
     return ok != 0;
@@ -95,14 +107,14 @@ __device__ __forceinline__ void elem(const T* x, int i, int j, T& re, T& im) {
 
 template <class T, int ADJA, int ADJB>
 __global__ void __launch_bounds__(kThreads) k_su3_mul(const T* __restrict__ A, const T* __restrict__ B,
-                                                      T* __restrict__ C, int64_t n) {
+                                                      T* __restrict__ C, int64_t n, unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sB = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar)) return;
+  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar, status)) return;
   if ((int)threadIdx.x < cnt) {
     T a[18], b[18], c[18];
 #pragma unroll
@@ -129,16 +141,16 @@ __global__ void __launch_bounds__(kThreads) k_su3_mul(const T* __restrict__ A, c
   stage_out(C + base * 18, sA, cnt * 18);
 }
 
-template <class T, int ADJ>
+template <class T, int ADJ, bool PROBE = false>
 __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A, const T* __restrict__ b,
-                                                         T* __restrict__ c, int64_t n) {
+                                                         T* __restrict__ c, int64_t n, unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sb = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  if (!stage_in(sA, A + base * 18, cnt * 18, sb, b + base * 6, cnt * 6, &bar)) return;
+  if (!stage_in<PROBE>(sA, A + base * 18, cnt * 18, sb, b + base * 6, cnt * 6, &bar, status)) return;
   if ((int)threadIdx.x < cnt) {
     T a[18], v[6], r[6];
 #pragma unroll
@@ -157,14 +169,14 @@ __global__ void __launch_bounds__(kThreads) k_su3_matvec(const T* __restrict__ A
 // mult_su3_mat_hwvec (ADJ 0) and mult_adj_su3_mat_hwvec (ADJ 1) of Table 1.
 template <class T, int ADJ>
 __global__ void __launch_bounds__(kThreads) k_su3_hwvec(const T* __restrict__ A, const T* __restrict__ h,
-                                                        T* __restrict__ c, int64_t n) {
+                                                        T* __restrict__ c, int64_t n, unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sh = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  if (!stage_in(sA, A + base * 18, cnt * 18, sh, h + base * 12, cnt * 12, &bar)) return;
+  if (!stage_in(sA, A + base * 18, cnt * 18, sh, h + base * 12, cnt * 12, &bar, status)) return;
   if ((int)threadIdx.x < cnt) {
     T a[18], v[12], r[12];
 #pragma unroll
@@ -184,14 +196,15 @@ __global__ void __launch_bounds__(kThreads) k_su3_hwvec(const T* __restrict__ A,
 
 // C = A + s B (scalar_mult_add_su3_matrix, Table 1); C may be A or B (same element).
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_su3_axpy(const T* A, const T* B, T* C, T sc, int64_t n) {
+__global__ void __launch_bounds__(kThreads) k_su3_axpy(const T* A, const T* B, T* C, T sc, int64_t n,
+                                                       unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   T* sA = reinterpret_cast<T*>(smem_raw);
   T* sB = sA + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar)) return;
+  if (!stage_in(sA, A + base * 18, cnt * 18, sB, B + base * 18, cnt * 18, &bar, status)) return;
   for (int i = threadIdx.x; i < cnt * 18; i += blockDim.x) sA[i] = fma(sc, sB[i], sA[i]);
   stage_out(C + base * 18, sA, cnt * 18);
 }
@@ -221,14 +234,15 @@ __device__ __forceinline__ void mat_mul(const T* A, const T* B, T* C) {
 // form, then s squarings (truncation below 1e-17 relative in FP64, 1e-9 in FP32).
 // reunit: rows 0 and 1 Gram-Schmidt, row 2 = conj(row0 x row1).
 template <class T, int KT>
-__global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U, T* out, T eps, int64_t n) {
+__global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U, T* out, T eps, int64_t n,
+                                                          unsigned int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   T* sP = reinterpret_cast<T*>(smem_raw);
   T* sU = sP + kThreads * 18;
   const int64_t base = (int64_t)blockIdx.x * kThreads;
   const int cnt = (int)min((int64_t)kThreads, n - base);
-  if (!stage_in(sP, P + base * 18, cnt * 18, sU, U + base * 18, cnt * 18, &bar)) return;
+  if (!stage_in(sP, P + base * 18, cnt * 18, sU, U + base * 18, cnt * 18, &bar, status)) return;
   if ((int)threadIdx.x < cnt) {
     T y[18], e[18], t[18];
 #pragma unroll
@@ -298,35 +312,173 @@ __global__ void __launch_bounds__(kThreads) k_su3_exp_mul(const T* P, const T* U
   stage_out(out + base * 18, sP, cnt * 18);
 }
 
+// ---- mat-vec with any storage: matrices of precision MP with R reals (18, or 12: rows 0
+// and 1, row 2 rebuilt as conj(row0 x row1)), vectors of precision VP; FP64 arithmetic for
+// FP64 matrices, FP32 otherwise.  Slices are staged by byte count (every item is a whole
+// number of 4-byte words), so the same bulk-copy path serves every format.
+
+// Brings bA bytes from gA and bB from gB into shared memory (as stage_in, by bytes).
+__device__ __forceinline__ bool stage_in_raw(void* sA, const void* gA, uint32_t bA, void* sB, const void* gB,
+                                             uint32_t bB, uint64_t* bar, unsigned int* status) {
+  __shared__ int ok;
+  if (bA % 16 == 0 && bB % 16 == 0 && aligned16(gA) && aligned16(gB)) {
+    if (threadIdx.x == 0) {
+      tma::mbar_init(bar, 1);
+      tma::mbar_expect_tx(bar, bA + bB);
+      tma::load(sA, gA, bA, bar);
+      tma::load(sB, gB, bB, bar);
+      ok = tma::mbar_wait(bar, 0);
+      if (!ok) {
+        atomicOr(status, kDevTmaTimeout);
+        tma::mbar_wait(bar, 0);
+      }
+    }
+    __syncthreads();
+    return ok != 0;
+  }
+  for (uint32_t i = threadIdx.x; i < bA / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(sA)[i] = __ldg(reinterpret_cast<const uint32_t*>(gA) + i);
+  for (uint32_t i = threadIdx.x; i < bB / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(sB)[i] = __ldg(reinterpret_cast<const uint32_t*>(gB) + i);
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ void stage_out_raw(void* gC, const void* sC, uint32_t bC) {
+  if (bC % 16 == 0 && aligned16(gC)) {
+    tma::fence_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma::store(gC, sC, bC);
+      tma::wait_all();
+    }
+  } else {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < bC / 4; i += blockDim.x)
+      reinterpret_cast<uint32_t*>(gC)[i] = reinterpret_cast<const uint32_t*>(sC)[i];
+  }
+}
+
+// n reals (n even) of storage precision P at p -> T, and back, in (re, im) pairs.
+template <lq_prec P, class T>
+__device__ __forceinline__ void get_reals(const void* p, int n, T* v) {
+  for (int k = 0; k < n / 2; ++k) {
+    if constexpr (P == LQ_F64) {
+      const double2 w = reinterpret_cast<const double2*>(p)[k];
+      v[2 * k] = (T)w.x; v[2 * k + 1] = (T)w.y;
+    } else if constexpr (P == LQ_F32) {
+      const float2 w = reinterpret_cast<const float2*>(p)[k];
+      v[2 * k] = (T)w.x; v[2 * k + 1] = (T)w.y;
+    } else {
+      const float2 w = Half16<P>::to_f2(reinterpret_cast<const uint32_t*>(p)[k]);
+      v[2 * k] = (T)w.x; v[2 * k + 1] = (T)w.y;
+    }
+  }
+}
+template <lq_prec P, class T>
+__device__ __forceinline__ void put_reals(void* p, int n, const T* v) {
+  for (int k = 0; k < n / 2; ++k) {
+    if constexpr (P == LQ_F64) reinterpret_cast<double2*>(p)[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+    else if constexpr (P == LQ_F32) reinterpret_cast<float2*>(p)[k] = make_float2((float)v[2 * k], (float)v[2 * k + 1]);
+    else reinterpret_cast<uint32_t*>(p)[k] = Half16<P>::from_f2((float)v[2 * k], (float)v[2 * k + 1]);
+  }
+}
+
+template <lq_prec MP, int R, lq_prec VP, int ADJ>
+__global__ void __launch_bounds__(kThreads) k_su3_matvec_ex(const void* __restrict__ A, const void* __restrict__ b,
+                                                            void* __restrict__ c, int64_t n, unsigned int* status) {
+  using T = typename std::conditional<MP == LQ_F64, double, float>::type;
+  constexpr uint32_t kMat = R * (MP == LQ_F64 ? 8 : MP == LQ_F32 ? 4 : 2);   // bytes per matrix
+  constexpr uint32_t kVec = 6 * (VP == LQ_F64 ? 8 : VP == LQ_F32 ? 4 : 2);   // bytes per vector
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  unsigned char* sA = smem_raw;
+  unsigned char* sb = smem_raw + kThreads * kMat;
+  const int64_t base = (int64_t)blockIdx.x * kThreads;
+  const int cnt = (int)min((int64_t)kThreads, n - base);
+  if (!stage_in_raw(sA, (const char*)A + base * kMat, cnt * kMat, sb, (const char*)b + base * kVec, cnt * kVec,
+                    &bar, status))
+    return;
+  if ((int)threadIdx.x < cnt) {
+    T u[18], v[6], r[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) r[k] = T(0);
+    get_reals<MP>(sA + threadIdx.x * kMat, R, u);
+    if (R == 12) reconstruct_row2(u);
+    get_reals<VP>(sb + threadIdx.x * kVec, 6, v);
+    if (ADJ) adj_mat_vec_add(u, v, r);
+    else mat_vec_add(u, v, r);
+    put_reals<VP>(sb + threadIdx.x * kVec, 6, r);
+  }
+  stage_out_raw((char*)c + base * kVec, sb, cnt * kVec);
+}
+
+template <lq_prec MP, int R, lq_prec VP>
+cudaError_t launch_matvec_ex(const void* A, const void* b, void* c, int64_t n, int adj, unsigned int* st,
+                             cudaStream_t s) {
+  constexpr size_t kMat = R * (MP == LQ_F64 ? 8 : MP == LQ_F32 ? 4 : 2);
+  constexpr size_t kVec = 6 * (VP == LQ_F64 ? 8 : VP == LQ_F32 ? 4 : 2);
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  const size_t smem = kThreads * (kMat + kVec);
+  if (adj) k_su3_matvec_ex<MP, R, VP, 1><<<blocks, kThreads, smem, s>>>(A, b, c, n, st);
+  else k_su3_matvec_ex<MP, R, VP, 0><<<blocks, kThreads, smem, s>>>(A, b, c, n, st);
+  return cudaGetLastError();
+}
+
+template <lq_prec MP, int R>
+cudaError_t matvec_ex_vec(const void* A, const void* b, void* c, int64_t n, int adj, lq_prec vp, unsigned int* st,
+                          cudaStream_t s) {
+  if constexpr (MP == LQ_F64) {
+    return vp == LQ_F64 ? launch_matvec_ex<MP, R, LQ_F64>(A, b, c, n, adj, st, s) : cudaErrorInvalidValue;
+  } else {
+    switch (vp) {
+      case LQ_F32: return launch_matvec_ex<MP, R, LQ_F32>(A, b, c, n, adj, st, s);
+      case LQ_BF16: return launch_matvec_ex<MP, R, LQ_BF16>(A, b, c, n, adj, st, s);
+      case LQ_F16: return launch_matvec_ex<MP, R, LQ_F16>(A, b, c, n, adj, st, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+}
+
+template <lq_prec MP>
+cudaError_t matvec_ex_recon(const void* A, const void* b, void* c, int64_t n, int adj, int recon, lq_prec vp,
+                            unsigned int* st, cudaStream_t s) {
+  return recon == 12 ? matvec_ex_vec<MP, 12>(A, b, c, n, adj, vp, st, s)
+                     : matvec_ex_vec<MP, 18>(A, b, c, n, adj, vp, st, s);
+}
+
 template <class T>
-cudaError_t launch_mul(const void* A, const void* B, void* C, int64_t n, int adjA, int adjB, cudaStream_t s) {
+cudaError_t launch_mul(const void* A, const void* B, void* C, int64_t n, int adjA, int adjB, unsigned int* st,
+                       cudaStream_t s) {
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   const size_t smem = 2 * kThreads * 18 * sizeof(T);
   const T* a = (const T*)A;
   const T* b = (const T*)B;
   T* c = (T*)C;
-  if (!adjA && !adjB) k_su3_mul<T, 0, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n);
-  else if (adjA && !adjB) k_su3_mul<T, 1, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n);
-  else if (!adjA && adjB) k_su3_mul<T, 0, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n);
-  else k_su3_mul<T, 1, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n);
+  if (!adjA && !adjB) k_su3_mul<T, 0, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n, st);
+  else if (adjA && !adjB) k_su3_mul<T, 1, 0><<<blocks, kThreads, smem, s>>>(a, b, c, n, st);
+  else if (!adjA && adjB) k_su3_mul<T, 0, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n, st);
+  else k_su3_mul<T, 1, 1><<<blocks, kThreads, smem, s>>>(a, b, c, n, st);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_matvec(const void* A, const void* b, void* c, int64_t n, int adj, cudaStream_t s) {
+cudaError_t launch_matvec(const void* A, const void* b, void* c, int64_t n, int adj, unsigned int* st,
+                          cudaStream_t s) {
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   const size_t smem = kThreads * 24 * sizeof(T);
-  if (adj) k_su3_matvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n);
-  else k_su3_matvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n);
+  if (adj) k_su3_matvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n, st);
+  else k_su3_matvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)b, (T*)c, n, st);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_hwvec(const void* A, const void* h, void* c, int64_t n, int adj, cudaStream_t s) {
+cudaError_t launch_hwvec(const void* A, const void* h, void* c, int64_t n, int adj, unsigned int* st,
+                         cudaStream_t s) {
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   const size_t smem = kThreads * 30 * sizeof(T);
-  if (adj) k_su3_hwvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n);
-  else k_su3_hwvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n);
+  if (adj) k_su3_hwvec<T, 1><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n, st);
+  else k_su3_hwvec<T, 0><<<blocks, kThreads, smem, s>>>((const T*)A, (const T*)h, (T*)c, n, st);
   return cudaGetLastError();
 }
 
@@ -351,7 +503,8 @@ extern "C" lq_status su3_mul_batch(lq_context* ctx, const void* A, const void* B
   if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "C overlaps A or B");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = prec == LQ_F64 ? launch_mul<double>(A, B, C, n, adjA, adjB, s) : launch_mul<float>(A, B, C, n, adjA, adjB, s);
+  cudaError_t e = prec == LQ_F64 ? launch_mul<double>(A, B, C, n, adjA, adjB, ctx->dev_status, s)
+                                 : launch_mul<float>(A, B, C, n, adjA, adjB, ctx->dev_status, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_mul");
   return LQ_OK;
 }
@@ -370,7 +523,8 @@ extern "C" lq_status su3_matvec_batch(lq_context* ctx, const void* A, const void
     return lq_fail(ctx, LQ_ERR_INVALID_ARG, "c overlaps A or b");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = prec == LQ_F64 ? launch_matvec<double>(A, b, c, n, adj, s) : launch_matvec<float>(A, b, c, n, adj, s);
+  cudaError_t e = prec == LQ_F64 ? launch_matvec<double>(A, b, c, n, adj, ctx->dev_status, s)
+                                 : launch_matvec<float>(A, b, c, n, adj, ctx->dev_status, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_matvec");
   return LQ_OK;
 }
@@ -389,7 +543,8 @@ extern "C" lq_status su3_mat_hwvec_batch(lq_context* ctx, const void* A, const v
     return lq_fail(ctx, LQ_ERR_INVALID_ARG, "c overlaps A or h");
   DeviceGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = prec == LQ_F64 ? launch_hwvec<double>(A, h, c, n, adj, s) : launch_hwvec<float>(A, h, c, n, adj, s);
+  cudaError_t e = prec == LQ_F64 ? launch_hwvec<double>(A, h, c, n, adj, ctx->dev_status, s)
+                                 : launch_hwvec<float>(A, h, c, n, adj, ctx->dev_status, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_hwvec");
   return LQ_OK;
 }
@@ -410,10 +565,10 @@ extern "C" lq_status su3_scalar_mult_add_batch(lq_context* ctx, const void* A, c
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   if (prec == LQ_F64)
     k_su3_axpy<double><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(double), st>>>(
-        (const double*)A, (const double*)B, (double*)C, s, n);
+        (const double*)A, (const double*)B, (double*)C, s, n, ctx->dev_status);
   else
     k_su3_axpy<float><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(float), st>>>(
-        (const float*)A, (const float*)B, (float*)C, (float)s, n);
+        (const float*)A, (const float*)B, (float*)C, (float)s, n, ctx->dev_status);
   LQ_CHECK_LAUNCH(ctx, "k_su3_axpy");
   return LQ_OK;
 }
@@ -434,10 +589,55 @@ extern "C" lq_status su3_exp_mul_batch(lq_context* ctx, const void* P, const voi
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   if (prec == LQ_F64)
     k_su3_exp_mul<double, 12><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(double), st>>>(
-        (const double*)P, (const double*)U, (double*)out, eps, n);
+        (const double*)P, (const double*)U, (double*)out, eps, n, ctx->dev_status);
   else
     k_su3_exp_mul<float, 7><<<blocks, kThreads, 2 * kThreads * 18 * sizeof(float), st>>>(
-        (const float*)P, (const float*)U, (float*)out, (float)eps, n);
+        (const float*)P, (const float*)U, (float*)out, (float)eps, n, ctx->dev_status);
   LQ_CHECK_LAUNCH(ctx, "k_su3_exp_mul");
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_selftest_wait_timeout(lq_context* ctx, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  DeviceGuard dg(ctx->device);
+  // one block of 128 items over buffers it never reads or writes: the probe issues no copy
+  void* buf = nullptr;
+  lq_status st = lq_scratch(ctx, (size_t)kThreads * 30 * sizeof(float), &buf);
+  if (st) return st;
+  float* f = (float*)buf;
+  k_su3_matvec<float, 0, true><<<1, kThreads, kThreads * 24 * sizeof(float), (cudaStream_t)stream>>>(
+      f, f + kThreads * 18, f + kThreads * 24, kThreads, ctx->dev_status);
+  LQ_CHECK_LAUNCH(ctx, "k_su3_matvec (wait self-test)");
+  return LQ_OK;
+}
+
+extern "C" lq_status su3_matvec_batch_ex(lq_context* ctx, const void* A, const void* b, void* c, int64_t n, int adj,
+                                         lq_prec mat_prec, lq_recon recon, lq_prec vec_prec, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (n < 0) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "n must be >= 0");
+  if (adj != 0 && adj != 1) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "adj must be 0 or 1");
+  if (mat_prec < LQ_F64 || mat_prec > LQ_F16 || vec_prec < LQ_F64 || vec_prec > LQ_F16)
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad precision");
+  if (recon != LQ_RECON_18 && recon != LQ_RECON_12) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "recon must be 18 or 12");
+  if ((mat_prec == LQ_F64) != (vec_prec == LQ_F64))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "LQ_F64 matrices pair with LQ_F64 vectors, reduced-precision matrices "
+                                            "with LQ_F32, LQ_BF16 or LQ_F16 vectors");
+  if (n == 0) return LQ_OK;
+  if (!A || !b || !c) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "NULL operand");
+  if (!lq_aligned16(A) || !lq_aligned16(b) || !lq_aligned16(c))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "operands must be 16-byte aligned");
+  const size_t mb = (size_t)n * (int)recon * lq_prec_bytes(mat_prec), vb = (size_t)n * 6 * lq_prec_bytes(vec_prec);
+  if (overlaps(c, vb, A, mb) || overlaps(c, vb, b, vb)) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "c overlaps A or b");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int* st = ctx->dev_status;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (mat_prec) {
+    case LQ_F64: e = matvec_ex_recon<LQ_F64>(A, b, c, n, adj, (int)recon, vec_prec, st, s); break;
+    case LQ_F32: e = matvec_ex_recon<LQ_F32>(A, b, c, n, adj, (int)recon, vec_prec, st, s); break;
+    case LQ_BF16: e = matvec_ex_recon<LQ_BF16>(A, b, c, n, adj, (int)recon, vec_prec, st, s); break;
+    case LQ_F16: e = matvec_ex_recon<LQ_F16>(A, b, c, n, adj, (int)recon, vec_prec, st, s); break;
+  }
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_su3_matvec_ex");
   return LQ_OK;
 }

@@ -3,9 +3,11 @@
 // slice per operand: one thread issues the copy, the copy engine moves it at full width,
 // and no thread spends registers or issue slots on the transfer.
 //
-// Every wait is bounded: after kMbarSpinLimit polls the waiting thread gives up, records
-// the event in the translation unit's `g_tma_timeouts` counter and the block skips its
-// work (its outputs are then left unwritten) instead of hanging the GPU.
+// Every wait is bounded: after kMbarSpinLimit polls the waiting thread gives up, sets a
+// flag in the context's device status word (lq_sync reports it as LQ_ERR_TIMEOUT), waits
+// once more, again bounded, so that the block does not leave while its own copies may
+// still be landing in its shared memory, and the block then skips its work (its outputs
+// are left unwritten) instead of hanging the GPU.
 #pragma once
 
 #include <stdint.h>
@@ -34,9 +36,9 @@ __device__ __forceinline__ void load(void* dst_smem, const void* src, uint32_t b
       : "memory");
 }
 
-// Bounded wait for phase `phase` of the barrier; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (long i = 0; i < kMbarSpinLimit; ++i) {
+// Bounded wait for phase `phase` of the barrier; false if `limit` polls did not see it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long limit = kMbarSpinLimit) {
+  for (long i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"

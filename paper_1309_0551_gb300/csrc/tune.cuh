@@ -112,6 +112,7 @@ struct CGScalars {
   double rr_prev; // ||r||^2 one iteration earlier (denominator of beta)
   double pAp;     // <p, M p>
   double alpha, beta;
+  double alpha_last;  // alpha of the last iteration in which the system was active
   double bb;      // ||b||^2
   double tol2;    // stop threshold on rr: tol^2 * bb
   double rhi2;    // ||r||^2 of the last FP64 residual replacement
@@ -135,6 +136,7 @@ __device__ __forceinline__ void finish_one(const Reducer& red, int rhs, double t
     case FIN_ALPHA:
       s->pAp = total;
       s->alpha = (s->active && total > 0.0) ? s->rr / total : 0.0;
+      if (s->active) s->alpha_last = s->alpha;
       break;
     case FIN_BETA:
       if (s->active) {
