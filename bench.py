@@ -11,7 +11,7 @@ and vectors whose total size exceeds three times the L2 cache, so no launch find
 links in L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f32 --recon 18]
-    python bench.py --impl reference       # the FP64 numpy oracle on the host cores
+    python bench.py --impl reference       # the FP64 C++ oracle on the host cores
 
 Under torchrun every rank runs its own replica (independent lattices, no collective on the
 data path); the value is the flops of all ranks over the slowest rank's time.
@@ -286,25 +286,76 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(dims, seconds=12.0):
-    """The oracle (numpy FP64, one thread of work per call) timed on the host: half Dslash
-    applications at the benchmark's lattice size until about `seconds` have passed."""
-    import synth
-    from oracle import dslash as odslash
-    U = synth.gauge_field(dims, "near_identity", seed=3, eps=0.3)
-    chi = synth.fermion_field(dims, 1, seed=2)[0]
-    Vh = synth.volume(dims) // 2
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or the platform's machine name."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_dslash_rate(cxx, U, chi, dims, threads, seconds):
+    """Half-Dslash applications of the C++ oracle on `threads` threads for about `seconds`:
+    (GFLOP/s, applications, elapsed)."""
+    Vh = synth_volume(dims) // 2
+    cxx.dslash_eo(U, chi, dims, 1, threads)   # warm-up (pages, thread pool)
     n, t0 = 0, time.perf_counter()
     while True:
-        odslash.dslash_eo(U, chi, dims, 1 - (n & 1))
+        cxx.dslash_eo(U, chi, dims, 1 - (n & 1), threads)
         n += 1
         dt = time.perf_counter() - t0
         if dt >= seconds:
             break
-    return {"value": round(n * Vh * FLOPS_PER_SITE / dt / 1e9, 4), "unit": "GFLOP/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{n} half-Dslash applications of the FP64 numpy oracle on the "
-                      f"{'x'.join(map(str, dims))} lattice ({dt:.1f} s)"}
+    return n * Vh * FLOPS_PER_SITE / dt / 1e9, n, dt
+
+
+def synth_volume(dims):
+    import synth
+    return synth.volume(dims)
+
+
+def cpu_baseline(dims, seconds=4.0, fp64_cg_iters=None):
+    """The FP64 C++ oracle (plain loops, OpenMP over sites) timed on the host: half-Dslash
+    applications at the benchmark's lattice size on one core and on every core (~`seconds`
+    each), and 50 iterations of its FP64 CG at 32^4 on every core (s/iteration; the time to
+    solution is extrapolated with the GPU's FP64 iteration count when given)."""
+    import synth
+    from oracle import cxx
+    U = synth.gauge_field(dims, "near_identity", seed=3, eps=0.3)
+    chi = synth.fermion_field(dims, 1, seed=2)[0]
+    nproc = os.cpu_count() or 1
+    threads = min(nproc, cxx.max_threads())
+    one, n1, dt1 = _oracle_dslash_rate(cxx, U, chi, dims, 1, seconds)
+    allc, na, dta = _oracle_dslash_rate(cxx, U, chi, dims, threads, seconds)
+    d4 = (32, 32, 32, 32)
+    U4 = synth.gauge_field(d4, "haar", seed=4)
+    b4 = synth.fermion_field(d4, 1, seed=5)[0]
+    t0 = time.perf_counter()
+    _, info = cxx.cg(U4, b4, 0.01, d4, tol=1e-30, maxiter=50, max_restarts=0, threads=threads)
+    s_it = (time.perf_counter() - t0) / info["iters"]
+    cg = {"workload": "32^4 Haar, m 0.01: FP64 CG of the C++ oracle, 50 iterations", "threads": threads,
+          "s_per_iter": round(s_it, 4)}
+    if fp64_cg_iters:
+        cg["extrapolated_seconds_to_1e-10"] = round(s_it * fp64_cg_iters, 1)
+        cg["extrapolated_with_iters"] = fp64_cg_iters
+    return {"value": round(allc, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(), "nproc": nproc,
+            "sample": f"{na} half-Dslash applications of the FP64 C++ oracle on the "
+                      f"{'x'.join(map(str, dims))} lattice on {threads} threads ({dta:.1f} s)",
+            "single_core": {"value": round(one, 3), "unit": "GFLOP/s", "cores": 1,
+                            "sample": f"{n1} half-Dslash applications on 1 thread ({dt1:.1f} s)"},
+            "cg_32c4": cg}
 
 
 def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64_peak=FP64_NOMINAL_GFLOPS):
@@ -722,16 +773,24 @@ def run_ours(args):
     if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == kernel_hash():
         traffic = NCU_TRAFFIC[key][0]
 
-    # ---- end to end: pinned host inputs copied in, outputs copied out, every step
+    # ---- end to end through the public API: every step copies its inputs in from pinned host
+    # memory, issues every half-Dslash as its own dslash_eo call through the binding and the C
+    # ABI (no graph: argument checks, tuning-table lookup and launch run per call), and copies
+    # the outputs back.
     host_in = [torch.empty_like(t, device="cpu").pin_memory() for t in ins]
     for h, t in zip(host_in, ins):
         h.copy_(t)
     host_out = [torch.empty_like(t, device="cpu").pin_memory() for t in outs]
+    side = [stream] + [torch.cuda.Stream() for _ in range(args.streams - 1)]
 
     def e2e_step():
         for h, t in zip(host_in, ins):
             t.copy_(h, non_blocking=True)
-        n = step()
+        for s_ in side[1:]:
+            s_.wait_stream(stream)
+        n = run_step(lq, ctx, gauges, ins, ts, outs, vc, side, nrhs=nrhs)
+        for s_ in side[1:]:
+            stream.wait_stream(s_)
         for h, t in zip(host_out, outs):
             h.copy_(t, non_blocking=True)
         return n
@@ -740,6 +799,18 @@ def run_ours(args):
     ms_e2e, _, _ = time_steps(torch, e2e_step, e2e_steps, min(args.warmup, 3), stream, dist, device)
     e2e_val = e2e_steps * APPS * 2 * Vh * nrhs * FLOPS_PER_SITE * world / (ms_e2e * 1e-3) / 1e9
     vbytes = ins[0].numel() * ins[0].element_size()
+
+    # the same with the step's launches replayed from a CUDA graph (copies still every step)
+    def e2e_graph_step():
+        for h, t in zip(host_in, ins):
+            t.copy_(h, non_blocking=True)
+        n = step()
+        for h, t in zip(host_out, outs):
+            h.copy_(t, non_blocking=True)
+        return n
+
+    ms_e2eg, _, _ = time_steps(torch, e2e_graph_step, e2e_steps, min(args.warmup, 3), stream, dist, device)
+    e2e_graph_val = e2e_steps * APPS * 2 * Vh * nrhs * FLOPS_PER_SITE * world / (ms_e2eg * 1e-3) / 1e9
 
     extra = {}
     if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
@@ -783,7 +854,10 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                      "us_per_launch": round(us_per_launch, 3)},
         "e2e": {"value": round(e2e_val, 1), "unit": "GFLOP/s", "h2d_bytes_per_step": K * vbytes,
-                "d2h_bytes_per_step": K * vbytes},
+                "d2h_bytes_per_step": K * vbytes,
+                "path": f"pinned host -> device copies, {2 * APPS} dslash_eo calls through the binding and "
+                        f"the C ABI on {args.streams} streams, device -> pinned host copies, every step",
+                "graph_replay_value": round(e2e_graph_val, 1)},
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -793,7 +867,8 @@ def run_ours(args):
     line["config"]["launch_shape"] = [l for l in ctx.tune_report().splitlines() if dkey in l]
     line.update(extra)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(DIMS)
+        fp64_iters = extra.get("cg", {}).get("fp64", {}).get("iters")
+        line["cpu_baseline"] = cpu_baseline(DIMS, fp64_cg_iters=fp64_iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -804,33 +879,37 @@ def run_ours(args):
 # ------------------------------------------------------------------ reference arm -----
 
 def run_reference(args):
-    """The oracle as it stands, on the host cores: each step is one half-Dslash application
-    of the FP64 numpy oracle on the benchmark lattice (a bounded sample of the workload)."""
+    """The oracle as it stands, on the host cores: each step is one full-D application (two
+    half-Dslash calls) of the FP64 C++ oracle on the benchmark lattice, on every core -- a
+    bounded sample of the GPU arm's step (100 applications)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import synth
-    from oracle import dslash as odslash
+    from oracle import cxx
     U = synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)
     chi = synth.fermion_field(DIMS, 1, seed=2)[0]
     Vh = synth.volume(DIMS) // 2
+    nproc = os.cpu_count() or 1
+    threads = min(nproc, cxx.max_threads())
     for i in range(args.warmup):
-        odslash.dslash_eo(U, chi, DIMS, 1 - (i & 1))
+        cxx.dslash_eo(U, cxx.dslash_eo(U, chi, DIMS, 1, threads), DIMS, 0, threads)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        odslash.dslash_eo(U, chi, DIMS, 1 - (i & 1))
+        cxx.dslash_eo(U, cxx.dslash_eo(U, chi, DIMS, 1, threads), DIMS, 0, threads)
     dt = time.perf_counter() - t0
-    value = args.steps * Vh * FLOPS_PER_SITE / dt / 1e9
-    sample = f"{args.steps} half-Dslash applications (one per step) on the 16x16x16x32 lattice"
+    value = args.steps * 2 * Vh * FLOPS_PER_SITE / dt / 1e9
+    sample = (f"{args.steps} full-D applications (two half-Dslash each, one application per step) on the "
+              f"16x16x16x32 lattice, FP64 C++ oracle on {threads} threads")
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1000 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": "staggered Dslash, 16^3x32 lattice, links exp(i*0.3*H) on SU(3)",
-                   "lattice": "16x16x16x32", "implementation": "FP64 numpy oracle on the host"},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                   "lattice": "16x16x16x32", "implementation": "FP64 C++ oracle (OpenMP) on the host"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "cpu": cpu_model(), "nproc": nproc, "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -839,7 +918,6 @@ def run_reference(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        os.environ.setdefault("OMP_NUM_THREADS", "1")
         run_reference(args)
     else:
         run_ours(args)

@@ -108,6 +108,15 @@ lq_status lq_selftest_wait_timeout(lq_context* ctx, lq_stream stream);
  * environment variable LQCD_DSLASH_SHAPE="block,rhs_tile,threads_per_site" forces one
  * shape for every Dslash launch it fits (block 64..256, a multiple of 32). */
 lq_status lq_set_tuning(lq_context* ctx, int mode);
+/* Persist the tuning table in the file `path` (NULL or "" stops persisting): the entries
+ * the file holds for this device (same name and SM count) are loaded now, without
+ * replacing shapes already in the table, and the table is saved to the file each time a
+ * new shape is tuned.  Two processes sharing the file then launch every kernel with the
+ * same shape -- the same summation order in every reduction, hence the same CG iterates
+ * and iteration counts.  lq_create does this itself when the environment variable
+ * LQCD_TUNE_CACHE names a file.  Processes that tune concurrently may overwrite each
+ * other's new entries (the last save wins); a lost entry is tuned again. */
+lq_status lq_set_tune_cache(lq_context* ctx, const char* path);
 /* Write the tuning table (one line per key: key, chosen block, rhs tile, microseconds)
  * into buf (NUL-terminated, truncated to len).  *needed receives the full length + 1. */
 lq_status lq_tune_report(const lq_context* ctx, char* buf, size_t len, size_t* needed);
@@ -134,6 +143,10 @@ lq_status lq_fp64_fma_rate(lq_context* ctx, double* gflops);
 lq_status lq_gauge_pack(lq_context* ctx, const int dims[4], const void* U_canon,
                         lq_prec prec, lq_recon recon, lq_gauge** out, lq_stream stream);
 lq_status lq_gauge_free(lq_context* ctx, lq_gauge* g);
+/* Re-pack a canonical complex128 field (device, [4][V][3][3], same lattice) into the
+ * existing gauge object g, keeping its precision and recon: no allocation, asynchronous on
+ * `stream` (work already queued that reads g must be ordered before it by the caller). */
+lq_status lq_gauge_repack(lq_context* ctx, lq_gauge* g, const void* U_canon, lq_stream stream);
 /* Bytes of device memory the packed field occupies (for bandwidth accounting). */
 lq_status lq_gauge_info(const lq_gauge* g, int dims[4], lq_prec* prec, lq_recon* recon,
                         size_t* bytes);
@@ -249,6 +262,46 @@ lq_status lq_long_links(lq_context* ctx, const int dims[4], const void* U_canon,
 lq_status dslash_wilson_eo(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
                            int out_parity, int nrhs, lq_prec vec_prec, int sign, lq_stream stream);
 
+/* -------------------------------------------------- t-split domain decomposition --- */
+/* A lattice (Lx, Ly, Lz, Lt) cut in t into P sub-domains of Lt/P (even) slices, one per
+ * process or GPU: the method's parallel mode (Table 4's parallel runs; the communication
+ * term of the timing model in Sec. 4), which the paper does not spell out.  Sub-domain k
+ * is packed as a lattice of its own, (Lx, Ly, Lz, Lt/P), from the slices
+ * [k Lt/P, (k+1) Lt/P) of the canonical fields (contiguous ranges: U[mu][t0 Vs : ...],
+ * one-parity vectors [t0 Vs/2 : ...], Vs = Lx Ly Lz).  Its half Dslash needs one face from
+ * each t neighbour (cyclic): the input on the next sub-domain's first slice and on the
+ * previous one's last slice -- the first / last Vs/2 sites of their own arrays, complex
+ * [nrhs][Vs/2][3] -- and, once, the previous sub-domain's U_t on its last slice.  The
+ * caller moves faces (NCCL send/recv, peer copies, ...) into buffers of its own device. */
+
+/* Attach the ghost links of a sub-domain to its gauge: Ut_ghost = device complex128
+ * [Vs][3][3], the previous sub-domain's U_t on its last slice in lex order within the slice
+ * (U_prev[3][(Lt/P - 1) Vs : Lt/P Vs]).  Stored in g's precision and recon (allocated on
+ * the first call, freed with g).  Asynchronous on stream. */
+lq_status lq_gauge_set_halo(lq_context* ctx, lq_gauge* g, const void* Ut_ghost, lq_stream stream);
+
+/* Half Dslash of a sub-domain: out = a1 w1 + c D in, D as in dslash_eo on the local
+ * lattice except that the t hops leaving it read ghost_fwd (forward hops from the last
+ * slice: the next sub-domain's first-slice face) and ghost_bwd with the ghost links
+ * (backward hops from the first slice: the previous sub-domain's last-slice face), each
+ * device complex [nrhs][Vs/2][3] of vec_prec.  With P = 1 (each sub-domain its own
+ * neighbour) it is dslash_eo.  U: a gauge with lq_gauge_set_halo done; vec_prec LQ_F64 for
+ * LQ_F64 links, LQ_F32 otherwise; w1 nullable (then a1 is ignored); out must not be in or
+ * w1.  One thread per output site and rhs.  570 flops per site and rhs. */
+lq_status dslash_eo_halo(lq_context* ctx, const lq_gauge* U, const void* in, const void* ghost_bwd,
+                         const void* ghost_fwd, void* out, int out_parity, int nrhs, lq_prec vec_prec,
+                         double a1, const void* w1, double c, lq_stream stream);
+
+/* Vector kernels for a solver driven by the caller (the t-split CG, whose inner products
+ * are summed across sub-domains between launches): on n complex values of prec (LQ_F64 or
+ * LQ_F32), y = a x + b y (y may be x) ... */
+lq_status lq_vec_axpby(lq_context* ctx, int64_t n, double a, const void* x, double b, void* y, lq_prec prec,
+                       lq_stream stream);
+/* ... and *result (device double) = Re<x, y>, each product and the sum in FP64 (fixed
+ * order for a given n: deterministic).  Uses the context's scratch space. */
+lq_status lq_vec_dot(lq_context* ctx, int64_t n, const void* x, const void* y, lq_prec prec, double* result,
+                     lq_stream stream);
+
 /* ---------------------------------------------------------------------- CG ---------- */
 
 typedef struct {
@@ -306,6 +359,21 @@ lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, 
  *   synchronise the stream.  Cost per call: two half Dslash and one pass over the links. */
 lq_status dslash_force(lq_context* ctx, const lq_gauge* U, double mass, const void* chi,
                        void* dSdU, void* force_TA, void* dSdchi, double* S, lq_stream stream);
+
+/* Leapfrog molecular dynamics for H = -1/2 sum Tr(P^2) + S(U), S = Re chi^dag M chi with chi
+ * held fixed (the integrator around the fermion force; the paper does not write it down):
+ *   P += eps/2 F(U);  then nsteps times: U = reunit(exp(eps P) U), P += eps F(U), the last
+ *   momentum step being eps/2 -- with F = TA(U G^dag) of dslash_force, the momentum update
+ *   scalar_mult_add_su3_matrix (Table 1) and the link update of su3_exp_mul_batch.
+ *   work: an LQ_F64, 18-real gauge object of the lattice, owned by the caller: the links
+ *         are re-packed into it (lq_gauge_repack) before every force evaluation.
+ *   U, P: device complex128 [4][V][3][3], updated in place; chi: device complex128 [Vh][3];
+ *   F: device complex128 [4][V][3][3] scratch for the force (caller-owned).
+ *   S: host, nullable: the action at the final links (the call then synchronises stream).
+ * No allocation per step (the force's work vectors live in the context's scratch space,
+ * grown on first use); every step runs in the library's kernels on `stream`. */
+lq_status md_leapfrog(lq_context* ctx, lq_gauge* work, void* U, void* P, const void* chi, double mass, double eps,
+                      int nsteps, void* F, double* S, lq_stream stream);
 
 /* Batched solve of nlat independent lattices (uneven sizes allowed, at most 16), each with
  * nrhs right-hand sides and its own mass: every system (lattice, rhs) runs the cg_solve

@@ -62,6 +62,7 @@ def load(path: str | None = None):
         "lq_last_error": ([P], ctypes.c_char_p),
         "lq_status_string": ([I], ctypes.c_char_p),
         "lq_set_tuning": ([P, I], I),
+        "lq_set_tune_cache": ([P, ctypes.c_char_p], I),
         "lq_fp64_fma_rate": ([P, ctypes.POINTER(D)], I),
         "lq_sync": ([P, P], I),
         "lq_inject_status": ([P, ctypes.c_uint, P], I),
@@ -69,6 +70,8 @@ def load(path: str | None = None):
         "lq_tune_report": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], I),
         "lq_gauge_pack": ([P, ctypes.POINTER(I), P, I, I, ctypes.POINTER(P), P], I),
         "lq_gauge_free": ([P, P], I),
+        "lq_gauge_repack": ([P, P, P, P], I),
+        "md_leapfrog": ([P, P, P, P, P, D, D, I, P, ctypes.POINTER(D), P], I),
         "lq_gauge_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                            ctypes.POINTER(ctypes.c_size_t)], I),
         "su3_mul_batch": ([P, P, P, P, L, I, I, I, P], I),
@@ -156,6 +159,10 @@ class Context:
     def selftest_wait_timeout(self, stream=None):
         """lq_selftest_wait_timeout: a bounded TMA wait that runs out with nothing in flight."""
         self.check(self.lib.lq_selftest_wait_timeout(self.handle, _stream(stream)))
+
+    def set_tune_cache(self, path):
+        """lq_set_tune_cache: load launch shapes from `path` and save new ones to it."""
+        self.check(self.lib.lq_set_tune_cache(self.handle, None if path is None else str(path).encode()))
 
     def fp64_fma_rate(self) -> float:
         """lq_fp64_fma_rate: measured FP64 FMA rate of the device in GFLOP/s."""
@@ -377,27 +384,26 @@ def dslash_force(ctx: Context, U: Gauge, mass: float, chi, dSdU=None, force_TA=N
     return S.value if want_S else None
 
 
-def md_leapfrog(ctx: Context, dims, U, P, chi, mass: float, eps: float, nsteps: int, stream=None):
+def lq_gauge_repack(ctx: Context, g: Gauge, U, stream=None):
+    """Re-pack the canonical complex128 field U into the existing gauge object g (no
+    allocation)."""
+    ctx.check(ctx.lib.lq_gauge_repack(ctx.handle, g.handle, _ptr(U), _stream(stream)))
+
+
+def md_leapfrog(ctx: Context, dims, U, P, chi, mass: float, eps: float, nsteps: int, work: Gauge | None = None,
+                F=None, stream=None):
     """Leapfrog molecular dynamics for H = -1/2 sum Tr(P^2) + Re chi^dag (m^2 - D^2) chi with
-    chi held fixed: P += eps/2 F; (U = reunit(exp(eps P) U); P += eps F) ..., the last momentum
-    half step eps/2.  U, P: canonical complex128 CUDA tensors (4, V, 3, 3), updated in place;
-    chi: (Vh, 3) complex128.  Every step runs in the library's kernels (dslash_force,
-    su3_exp_mul_batch, su3_scalar_mult_add_batch).  Returns the final action S."""
+    chi held fixed (C entry point md_leapfrog): P += eps/2 F; (U = reunit(exp(eps P) U);
+    P += eps F) ..., the last momentum half step eps/2.  U, P: canonical complex128 CUDA
+    tensors (4, V, 3, 3), updated in place; chi: (Vh, 3) complex128.  ``work`` (an FP64
+    18-real Gauge of the lattice) and ``F`` (a tensor like U) are reused across calls when
+    given.  Returns the final action S."""
     import torch
-    n = U.numel() // 9
-    F = torch.empty_like(U)
-
-    def force():
-        g = lq_gauge_pack(ctx, dims, U, LQ_F64, 18, stream)
-        S = dslash_force(ctx, g, mass, chi, force_TA=F, want_S=True, stream=stream)
-        g.free()
-        return S
-
-    force()
-    su3_scalar_mult_add_batch(ctx, P, F, P, 0.5 * eps, n, LQ_F64, stream)
-    S = None
-    for k in range(nsteps):
-        su3_exp_mul_batch(ctx, P, U, U, eps, n, LQ_F64, stream)
-        S = force()
-        su3_scalar_mult_add_batch(ctx, P, F, P, eps if k < nsteps - 1 else 0.5 * eps, n, LQ_F64, stream)
-    return S
+    if work is None:
+        work = lq_gauge_pack(ctx, dims, U, LQ_F64, 18, stream)
+    if F is None:
+        F = torch.empty_like(U)
+    S = ctypes.c_double(0.0)
+    ctx.check(ctx.lib.md_leapfrog(ctx.handle, work.handle, _ptr(U), _ptr(P), _ptr(chi), float(mass), float(eps),
+                                  int(nsteps), _ptr(F), ctypes.byref(S), _stream(stream)))
+    return S.value

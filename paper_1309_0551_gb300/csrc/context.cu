@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <string>
 
@@ -67,6 +68,11 @@ extern "C" lq_status lq_create(lq_context** out, int device) {
     delete ctx;
     return LQ_ERR_CUDA;
   }
+  char tag[320];
+  snprintf(tag, sizeof tag, "%s/%d", prop.name, prop.multiProcessorCount);
+  for (char* c = tag; *c; ++c)
+    if (*c == ' ' || *c == '\t') *c = '_';
+  ctx->device_tag = tag;
   const char* env = getenv("LQCD_TUNE");
   ctx->tuning = !(env && env[0] == '0');
   // "block,rhs_tile,threads_per_site", e.g. "128,1,2": every Dslash launch whose right-hand
@@ -80,7 +86,61 @@ extern "C" lq_status lq_create(lq_context** out, int device) {
       ctx->forced.tps = p;
     }
   }
+  const char* cache = getenv("LQCD_TUNE_CACHE");
+  if (cache && cache[0]) lq_set_tune_cache(ctx, cache);
   *out = ctx;
+  return LQ_OK;
+}
+
+// Tuning cache file: one entry per line, "<device tag>\t<key>\t<block> <rhs_tile> <tps> <us>".
+// Loading keeps the entries of this device (name and SM count) and leaves entries already
+// in the table alone; saving rewrites the file (through a temporary file and a rename) with
+// this context's entries plus the other devices' lines it found.
+static void tune_load(lq_context* ctx, const std::string& path) {
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    char* t1 = strchr(line, '\t');
+    if (!t1) continue;
+    char* t2 = strchr(t1 + 1, '\t');
+    if (!t2) continue;
+    *t1 = 0;
+    *t2 = 0;
+    if (ctx->device_tag != line) continue;
+    TuneEntry e;
+    if (sscanf(t2 + 1, "%d %d %d %f", &e.block, &e.rhs_tile, &e.tps, &e.us) != 4 || e.block <= 0) continue;
+    ctx->tune.emplace(std::string(t1 + 1), e);
+  }
+  fclose(f);
+}
+
+void lq_tune_save(lq_context* ctx) {
+  if (ctx->tune_cache.empty()) return;
+  std::string others;
+  if (FILE* f = fopen(ctx->tune_cache.c_str(), "r")) {
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+      const char* t1 = strchr(line, '\t');
+      if (t1 && std::string(line, t1 - line) != ctx->device_tag) others += line;
+    }
+    fclose(f);
+  }
+  const std::string tmp = ctx->tune_cache + ".tmp" + std::to_string((long)getpid());
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fputs(others.c_str(), f);
+  for (const auto& kv : ctx->tune)
+    fprintf(f, "%s\t%s\t%d %d %d %.3f\n", ctx->device_tag.c_str(), kv.first.c_str(), kv.second.block,
+            kv.second.rhs_tile, kv.second.tps, kv.second.us);
+  fclose(f);
+  rename(tmp.c_str(), ctx->tune_cache.c_str());
+}
+
+extern "C" lq_status lq_set_tune_cache(lq_context* ctx, const char* path) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  ctx->tune_cache = path ? path : "";
+  if (!ctx->tune_cache.empty()) tune_load(ctx, ctx->tune_cache);
   return LQ_OK;
 }
 
@@ -219,6 +279,8 @@ static size_t bytes_per_link(lq_prec p, int r) {
   return 0;
 }
 
+static cudaError_t pack_into(lq_gauge* g, const void* U_canon, cudaStream_t s);
+
 extern "C" lq_status lq_gauge_pack(lq_context* ctx, const int dims[4], const void* U_canon,
                                    lq_prec prec, lq_recon recon, lq_gauge** out, lq_stream stream) {
   if (!ctx) return LQ_ERR_INVALID_ARG;
@@ -247,6 +309,29 @@ extern "C" lq_status lq_gauge_pack(lq_context* ctx, const int dims[4], const voi
   cudaStream_t s = (cudaStream_t)stream;
   e = cudaMemsetAsync(g->data, 0, g->bytes, s);
   if (e != cudaSuccess) { cudaFree(g->data); delete g; return lq_cuda_fail(ctx, e, "cudaMemsetAsync(gauge)"); }
+  e = pack_into(g, U_canon, s);
+  if (e != cudaSuccess) { cudaFree(g->data); delete g; return lq_cuda_fail(ctx, e, "k_gauge_pack"); }
+  *out = g;
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_gauge_repack(lq_context* ctx, lq_gauge* g, const void* U_canon, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (!g) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "gauge is NULL");
+  if (!U_canon || !lq_aligned16(U_canon))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "U must be a non-NULL 16-byte aligned device pointer");
+  DeviceGuard dg(ctx->device);
+  cudaError_t e = pack_into(g, U_canon, (cudaStream_t)stream);
+  if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_gauge_pack");
+  return LQ_OK;
+}
+
+// Launches the packing kernel of g's format over the canonical field U (the padding of the
+// planes is left as it is).
+static cudaError_t pack_into(lq_gauge* g, const void* U_canon, cudaStream_t s) {
+  const int V = 2 * g->Vh;
+  const lq_prec prec = g->prec;
+  const int recon = (int)g->recon;
   Geom G = make_geom(g);
   dim3 block(256), grid((V + 255) / 256, 4);
 #define LQ_PACK(P, R) k_gauge_pack<P, R><<<grid, block, 0, s>>>((const double*)U_canon, g->data, G, g->blk_bytes, V)
@@ -266,10 +351,7 @@ extern "C" lq_status lq_gauge_pack(lq_context* ctx, const int dims[4], const voi
     }
   }
 #undef LQ_PACK
-  e = cudaGetLastError();
-  if (e != cudaSuccess) { cudaFree(g->data); delete g; return lq_cuda_fail(ctx, e, "k_gauge_pack"); }
-  *out = g;
-  return LQ_OK;
+  return cudaGetLastError();
 }
 
 extern "C" lq_status lq_gauge_free(lq_context* ctx, lq_gauge* g) {
@@ -279,8 +361,71 @@ extern "C" lq_status lq_gauge_free(lq_context* ctx, lq_gauge* g) {
   // The field may still be read by queued work on any stream.
   cudaDeviceSynchronize();
   cudaError_t e = cudaFree(g->data);
+  if (g->halo) cudaFree(g->halo);
   delete g;
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "cudaFree(gauge)");
+  return LQ_OK;
+}
+
+// Ghost links of a t-split sub-domain: canonical complex128 U_t of the previous
+// sub-domain's last slice, Vs = Lx Ly Lz links in lex order within the slice, into two
+// blocks by the parity of the ghost site (x + y + z + 1: it sits at local t = -1), at
+// within-face index lex_s >> 1.
+template <lq_prec P, int R>
+__global__ void k_halo_pack(const double* __restrict__ Ut, char* __restrict__ out, int Lx, int Ly, int Vs, int S,
+                            size_t blk_bytes) {
+  const int ls = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ls >= Vs) return;
+  const int x = ls % Lx, y = (ls / Lx) % Ly, z = ls / (Lx * Ly);
+  const int par = (x + y + z + 1) & 1;
+  const double2* src = reinterpret_cast<const double2*>(Ut) + (size_t)ls * 9;
+  double u[18];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 v = src[k];
+    u[2 * k] = v.x;
+    u[2 * k + 1] = v.y;
+  }
+  LinkT<P, R>::store(out + (size_t)par * blk_bytes, S, ls >> 1, u);
+}
+
+extern "C" lq_status lq_gauge_set_halo(lq_context* ctx, lq_gauge* g, const void* Ut_ghost, lq_stream stream) {
+  if (!ctx) return LQ_ERR_INVALID_ARG;
+  if (!g || !Ut_ghost || !lq_aligned16(Ut_ghost))
+    return lq_fail(ctx, LQ_ERR_INVALID_ARG, "gauge and a 16-byte aligned ghost-link pointer are required");
+  DeviceGuard dg(ctx->device);
+  const int Vs = g->dims[0] * g->dims[1] * g->dims[2];
+  const int S = (Vs / 2 + 31) / 32 * 32;
+  size_t blk = (size_t)S * bytes_per_link(g->prec, g->recon);
+  blk = (blk + 255) / 256 * 256;
+  if (!g->halo) {
+    LQ_CUDA(ctx, cudaMalloc(&g->halo, 2 * blk));
+    g->halo_blk_bytes = blk;
+    g->halo_S = S;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  LQ_CUDA(ctx, cudaMemsetAsync(g->halo, 0, 2 * blk, s));
+  const dim3 grid((Vs + 255) / 256), block(256);
+  const double* U = (const double*)Ut_ghost;
+  const int Lx = g->dims[0], Ly = g->dims[1];
+#define LQ_HPACK(P, R) k_halo_pack<P, R><<<grid, block, 0, s>>>(U, g->halo, Lx, Ly, Vs, S, blk)
+  if (g->recon == 18) {
+    switch (g->prec) {
+      case LQ_F64: LQ_HPACK(LQ_F64, 18); break;
+      case LQ_F32: LQ_HPACK(LQ_F32, 18); break;
+      case LQ_BF16: LQ_HPACK(LQ_BF16, 18); break;
+      case LQ_F16: LQ_HPACK(LQ_F16, 18); break;
+    }
+  } else {
+    switch (g->prec) {
+      case LQ_F64: LQ_HPACK(LQ_F64, 12); break;
+      case LQ_F32: LQ_HPACK(LQ_F32, 12); break;
+      case LQ_BF16: LQ_HPACK(LQ_BF16, 12); break;
+      case LQ_F16: LQ_HPACK(LQ_F16, 12); break;
+    }
+  }
+#undef LQ_HPACK
+  LQ_CHECK_LAUNCH(ctx, "k_halo_pack");
   return LQ_OK;
 }
 

@@ -47,8 +47,13 @@ struct lq_context {
   void* flush = nullptr;        // buffer larger than L2, written between tuning timings
   size_t flush_bytes = 0;
   TuneEntry forced;             // Dslash launch shape forced by LQCD_DSLASH_SHAPE (block 0: none)
+  std::string tune_cache;       // file the tuning table is loaded from and saved to ("" = none)
+  std::string device_tag;       // "<device name>/<SM count>": entries of other devices are ignored
   std::mutex mu;
 };
+
+// Save the context's tuning table to its cache file (no-op without one).
+void lq_tune_save(lq_context* ctx);
 
 struct lq_gauge {
   int dims[4];
@@ -59,6 +64,12 @@ struct lq_gauge {
   size_t blk_bytes;   // bytes of one (direction, parity) block
   size_t bytes;       // 8 blocks
   char* data;
+  // t-split domain decomposition (lq_gauge_set_halo): U_t on the last slice of the previous
+  // sub-domain, the backward links of this sub-domain's first slice, in this gauge's format:
+  // two blocks (parity of the ghost site) of halo_S chunks per plane; NULL when not set.
+  char* halo = nullptr;
+  size_t halo_blk_bytes = 0;
+  int halo_S = 0;
 };
 
 // Status helpers ------------------------------------------------------------------------

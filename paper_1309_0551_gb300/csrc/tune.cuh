@@ -100,6 +100,7 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
     }
   }
   ctx->tune[key] = best;
+  lq_tune_save(ctx);
   *pick = best;
   return LQ_OK;
 }
