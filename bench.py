@@ -816,7 +816,7 @@ def run_ours(args):
     if rank == 0 and not args.no_variants:  # same regime as the headline: concurrent launches
         fp64 = ctx.fp64_fma_rate()
         extra["fp64_peak"] = {"gflops": round(fp64, 1), "nominal_gflops": FP64_NOMINAL_GFLOPS,
-                              "source": "measured: lq_fp64_fma_rate (8 independent FMA chains per thread, "
+                              "source": "measured: lq_fp64_fma_rate (16 independent FMA chains per thread, "
                                         "every SM, CUDA events, best of 3)"}
         U_var = U_dev if dims == DIMS else torch.from_numpy(
             synth.gauge_field(DIMS, "near_identity", seed=3, eps=0.3)).cuda()

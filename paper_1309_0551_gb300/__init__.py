@@ -71,6 +71,10 @@ def load(path: str | None = None):
         "lq_gauge_pack": ([P, ctypes.POINTER(I), P, I, I, ctypes.POINTER(P), P], I),
         "lq_gauge_free": ([P, P], I),
         "lq_gauge_repack": ([P, P, P, P], I),
+        "lq_gauge_set_halo": ([P, P, P, P], I),
+        "dslash_eo_halo": ([P, P, P, P, P, P, I, I, I, D, P, D, P], I),
+        "lq_vec_axpby": ([P, L, D, P, D, P, I, P], I),
+        "lq_vec_dot": ([P, L, P, P, I, P, P], I),
         "md_leapfrog": ([P, P, P, P, P, D, D, I, P, ctypes.POINTER(D), P], I),
         "lq_gauge_info": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                            ctypes.POINTER(ctypes.c_size_t)], I),
@@ -388,6 +392,34 @@ def lq_gauge_repack(ctx: Context, g: Gauge, U, stream=None):
     """Re-pack the canonical complex128 field U into the existing gauge object g (no
     allocation)."""
     ctx.check(ctx.lib.lq_gauge_repack(ctx.handle, g.handle, _ptr(U), _stream(stream)))
+
+
+def lq_gauge_set_halo(ctx: Context, g: Gauge, Ut_ghost, stream=None):
+    """Attach the ghost links of a t-split sub-domain: the previous sub-domain's U_t on its
+    last slice, a contiguous complex128 CUDA tensor (Vs, 3, 3)."""
+    ctx.check(ctx.lib.lq_gauge_set_halo(ctx.handle, g.handle, _ptr(Ut_ghost), _stream(stream)))
+
+
+def dslash_eo_halo(ctx: Context, U: Gauge, inp, ghost_bwd, ghost_fwd, out, out_parity: int, nrhs: int = 1,
+                   a1: float = 0.0, w1=None, c: float = 1.0, vec_prec=None, stream=None):
+    """out = a1 w1 + c D inp on a t-split sub-domain, the t hops leaving it reading the ghost
+    faces (complex [nrhs][Vs/2][3] tensors) and the gauge's ghost links."""
+    vp = vec_prec_of(inp) if vec_prec is None else vec_prec
+    ctx.check(ctx.lib.dslash_eo_halo(ctx.handle, U.handle, _ptr(inp), _ptr(ghost_bwd), _ptr(ghost_fwd), _ptr(out),
+                                     int(out_parity), int(nrhs), int(vp), float(a1), _ptr(w1), float(c),
+                                     _stream(stream)))
+
+
+def lq_vec_axpby(ctx: Context, a: float, x, b: float, y, stream=None):
+    """y = a x + b y over a whole complex tensor (complex128 or complex64)."""
+    ctx.check(ctx.lib.lq_vec_axpby(ctx.handle, int(x.numel()), float(a), _ptr(x), float(b), _ptr(y),
+                                   vec_prec_of(x), _stream(stream)))
+
+
+def lq_vec_dot(ctx: Context, x, y, result, stream=None):
+    """result (a float64 CUDA tensor of one element) = Re<x, y>, summed in FP64."""
+    ctx.check(ctx.lib.lq_vec_dot(ctx.handle, int(x.numel()), _ptr(x), _ptr(y), vec_prec_of(x), _ptr(result),
+                                 _stream(stream)))
 
 
 def md_leapfrog(ctx: Context, dims, U, P, chi, mass: float, eps: float, nsteps: int, work: Gauge | None = None,

@@ -7,7 +7,7 @@
 
 namespace {
 
-constexpr int kChains = 8;      // independent FMA chains per thread (hide the pipe latency)
+constexpr int kChains = 16;     // independent FMA chains per thread (hide the pipe latency)
 constexpr int kFmaThreads = 256;
 
 // Each thread runs kChains independent chains a <- a * b + c for `iters` steps; the values
@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(kFmaThreads) k_fma64(int iters, double b, doub
   double a[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+#pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
@@ -36,7 +37,7 @@ extern "C" lq_status lq_fp64_fma_rate(lq_context* ctx, double* gflops) {
   LQ_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma64, kFmaThreads, 0));
   if (per_sm < 1) per_sm = 1;
   const int blocks = ctx->num_sms * per_sm;
-  const int iters = 1 << 14;
+  const int iters = 1 << 13;
   void* sink = nullptr;
   lq_status st = lq_scratch(ctx, sizeof(double) * blocks, &sink);
   if (st) return st;
