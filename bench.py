@@ -87,7 +87,8 @@ def parse():
                    help="independent applications in flight (graph branches)")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--variants", default="all",
-                   help="comma-separated variant groups: formats, l2_warm, 32c4, improved, wilson, multi_rhs, su3")
+                   help="comma-separated variant groups: formats, l2_warm, 32c4, lone, improved, wilson, "
+                        "multi_rhs, su3")
     p.add_argument("--no-cg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cg-maxiter", type=int, default=20000,
@@ -360,7 +361,7 @@ def cpu_baseline(dims, seconds=4.0, fp64_cg_iters=None):
 
 def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64_peak=FP64_NOMINAL_GFLOPS):
     """The per-format, operator and SU(3)-batch lines; `groups` (comma-separated, or "all")
-    picks among formats, l2_warm, 32c4, improved, wilson, multi_rhs, su3."""
+    picks among formats, l2_warm, 32c4, lone, improved, wilson, multi_rhs, su3."""
     import synth
     sel = set(groups.split(","))
 
@@ -427,6 +428,30 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             torch.cuda.empty_cache()
         del U4
         torch.cuda.empty_cache()
+    if want("lone"):
+        # one stream: each half Dslash waits for the previous one (the way a solver issues
+        # them), so a launch's ramp-up and tail are not hidden by other launches in flight
+        for prec, recon, vec, dims in (("f32", 18, "f32", DIMS), ("bf16", 12, "bf16", DIMS),
+                                       ("f32", 12, "f32", (32, 32, 32, 32)),
+                                       ("bf16", 12, "bf16", (32, 32, 32, 32))):
+            Vhl = synth.volume(dims) // 2
+            Ul = U_dev if dims == DIMS else torch.from_numpy(
+                synth.gauge_field(dims, "near_identity", seed=3, eps=0.3)).cuda()
+            sb = site_bytes(prec, recon, vec)
+            K = ring_size(Vhl * sb, l2, 1)
+            gauges, ins, ts, outs = make_ring(lq, ctx, Ul, dims, prec, recon, vec, K)
+            vc = lq.PREC[vec]
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), 1)
+            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+            del g
+            us = ms * 1000.0 / launches
+            gbs = Vhl * sb / us / 1e3
+            out[f"lone/{prec}/{recon}/{vec}/{'x'.join(map(str, dims))}"] = {
+                "gflops": round(Vhl * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+                "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K,
+                "streams": 1}
+            del gauges, ins, ts, outs, Ul
+            torch.cuda.empty_cache()
     if want("improved"):
         # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
         for prec in ("f32", "bf16"):
@@ -527,22 +552,24 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             del gauges, ins, ts, outs
             torch.cuda.empty_cache()
     if want("su3"):
-        # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice
+        # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice; like the
+        # Dslash lines, `nstreams` independent batches in flight (graph branches), each
+        # launch on its own ring copy (inputs larger than L2)
         n = 4 * 2 * Vh
         A = torch.from_numpy(synth.haar_su3(synth.rng(9), n))
         b = torch.from_numpy(synth.complex_gaussian(synth.rng(10), (n, 3)))
         for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
             per = n * 30 * BYTES[prec]
-            K = ring_size(per, l2)
+            K = ring_size(per, l2, nstreams)
             As = [A.to(dt).cuda() for _ in range(K)]
             bs = [b.to(dt).cuda() for _ in range(K)]
             cs = [torch.empty_like(bs[0]) for _ in range(K)]
             for adj in (0, 1):
                 def step(ss):
                     for i in range(20):
-                        lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[0])
+                        lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[i % len(ss)])
                     return 20
-                g = GraphStep(torch, step, 1)
+                g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
                 us = ms * 1000.0 / launches
@@ -554,7 +581,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
         for mat, recon, vec in (("f64", 12, "f64"), ("f32", 12, "f32"), ("bf16", 18, "bf16"),
                                 ("bf16", 12, "bf16"), ("f16", 12, "f16"), ("bf16", 12, "f32")):
             per = n * (recon * BYTES[mat] + 12 * BYTES[vec])
-            K = ring_size(per, l2)
+            K = ring_size(per, l2, nstreams)
             rows = A[:, :2, :].contiguous() if recon == 12 else A
 
             def dev(z, prec):
@@ -570,9 +597,10 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             for adj in (0, 1):
                 def step(ss, As=As, bs=bs, cs=cs, mat=mat, recon=recon, vec=vec, adj=adj):
                     for i in range(20):
-                        lq.su3_matvec_batch_ex(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, mat, recon, vec, ss[0])
+                        lq.su3_matvec_batch_ex(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, mat, recon, vec,
+                                               ss[i % len(ss)])
                     return 20
-                g = GraphStep(torch, step, 1)
+                g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
                 us = ms * 1000.0 / launches
@@ -586,16 +614,16 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
         B2 = torch.from_numpy(synth.haar_su3(synth.rng(11), n))
         for prec, dt in (("f64", torch.complex128), ("f32", torch.complex64)):
             per = n * 54 * BYTES[prec]
-            K = ring_size(per, l2)
+            K = ring_size(per, l2, nstreams)
             As = [A.to(dt).cuda() for _ in range(K)]
             Bs = [B2.to(dt).cuda() for _ in range(K)]
             Cs = [torch.empty_like(As[0]) for _ in range(K)]
             for adjA, adjB in ((0, 0), (1, 0), (0, 1)):
                 def step(ss):
                     for i in range(20):
-                        lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[0])
+                        lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[i % len(ss)])
                     return 20
-                g = GraphStep(torch, step, 1)
+                g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
                 us = ms * 1000.0 / launches

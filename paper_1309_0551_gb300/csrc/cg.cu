@@ -69,10 +69,10 @@ template <> struct Chunk<LQ_F64> {
 // partials of the preceding D_eo launch (FIN_DEFER, `cols` per rhs), summed here once in a
 // fixed order.  A separate one-block launch: were every block of the update kernel to sum
 // them, all of its blocks would hammer the same few L2 lines.
-__global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, int cols, CGScalars* sc) {
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, size_t stride, int cols, CGScalars* sc) {
   pdl_wait();
   const int rhs = blockIdx.x;
-  const double pAp = block_total(pap + (size_t)rhs * cols, cols);
+  const double pAp = block_total(pap + (size_t)rhs * stride, cols);
   if (threadIdx.x == 0) {
     CGScalars* s = sc + rhs;
     s->pAp = pAp;
@@ -489,14 +489,24 @@ lq_status batch_iteration_dslash(Solver& S) {
   MultiKArgs d = multi_args(S, false, 1, S.p, S.t);
   lq_status st = launch_dslash_multi(S.ctx, d, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
   if (st) return st;
+  // Ap = m^2 p - D_eo t with <p, Ap>: per-block row partials only (FIN_DEFER), summed by
+  // k_cg_alpha with one block per system (a last-block finisher would sum every row alone)
   MultiKArgs e = multi_args(S, false, 0, S.t, S.Ap, S.p);
   for (int l = 0; l < B.nlat; ++l) e.lat[l].a1 = B.mass[l] * B.mass[l];
   e.c = -1.0;
   e.reduce = RED_DOT;
-  e.red = S.reducer(FIN_ALPHA);
+  e.red = S.reducer(FIN_DEFER);
+  e.red.partials = S.dpartials;
   e.skip_state = S.sc;
   e.skip_mode = SKIP_INACTIVE;
-  return launch_dslash_multi(S.ctx, e, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
+  int cols = 0;
+  e.cols_out = &cols;
+  st = launch_dslash_multi(S.ctx, e, g0->prec, g0->recon, S.vp, B.key_lo, S.s);
+  if (st) return st;
+  if (cols < 1) return lq_fail(S.ctx, LQ_ERR_INVALID_ARG, "internal: empty reduction launch");
+  k_cg_alpha<<<S.nsys, 1024, 0, S.s>>>(S.dpartials, e.pstride, cols, S.sc);
+  LQ_CHECK_LAUNCH(S.ctx, "k_cg_alpha");
+  return LQ_OK;
 }
 
 // skip_done: leave out the lattices whose systems have all met the tolerance already
@@ -598,7 +608,7 @@ lq_status iteration(Solver& S) {
   st = launch_dslash(S.ctx, e, S.s);
   if (st) return st;
   cudaError_t ce = launch_k(k_cg_alpha, dim3(S.nrhs), dim3(1024), 0, S.s, S.pdl, (const double*)S.dpartials,
-                            red.cols, S.sc);
+                            (size_t)red.cols, red.cols, S.sc);
   if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cg_alpha");
   return launch_blas_update(S);
 }
@@ -1215,7 +1225,7 @@ extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge*
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = 5 * vin + 4 * v64 + S.nsys * (sizeof(CGScalars) + 16) + 8 +
-                      2 * (size_t)S.nsys * S.nblocks_max * sizeof(double) + 14 * 256;
+                      3 * (size_t)S.nsys * S.nblocks_max * sizeof(double) + 15 * 256;
   void* base = nullptr;
   lq_status st = lq_scratch(ctx, need, &base);
   if (st) return st;
@@ -1233,6 +1243,7 @@ extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge*
   S.result = (double*)A.take(sizeof(double) * 2 * S.nsys);
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * 2 * S.nsys * S.nblocks_max);
+  S.dpartials = (double*)A.take(sizeof(double) * S.nsys * S.nblocks_max);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   st = host_scalars(ctx, S.nsys);
   if (st) return st;

@@ -69,6 +69,13 @@ static std::vector<TuneEntry> dslash_candidates(lq_prec gp, int nrhs) {
   return c;
 }
 
+// Columns of per-block partials a reduction launch of this shape stores per rhs: its site
+// blocks (32 sites per block for the rhs-per-warp kernel).
+static int dslash_partial_cols(int Vh, const TuneEntry& c) {
+  if (c.tps == kTpsRhsWarps) return (Vh + 31) / 32;
+  return (int)(((long long)Vh * c.tps + c.block - 1) / c.block);
+}
+
 static DslashKArgs make_kargs(const DslashArgs& a) {
   DslashKArgs k;
   k.gauge = a.U->data;
@@ -109,8 +116,10 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   }
   TuneEntry pick;
   const TuneEntry& f = ctx->forced;
-  // the rhs-per-warp kernel: FP32 vectors, no fused reduction, two or more rhs
-  const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.reduce == RED_NONE && a.nrhs >= 2;
+  // the rhs-per-warp kernel: FP32 vectors, two or more rhs, a fused reduction only as
+  // deferred per-block partials (FIN_DEFER)
+  const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.nrhs >= 2 &&
+                     (a.reduce == RED_NONE || (a.red && a.red->finisher == FIN_DEFER));
   if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
       !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && dslash_rw_shape_ok(f.block, f.rhs_tile)))) {
     pick = f;
@@ -130,7 +139,7 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
       key += a.reduce == RED_DOT ? " red=dot" : " red=norm";
       std::vector<TuneEntry> fit;  // every candidate must fit the reduction scratch
       for (const TuneEntry& c : cands)
-        if (a.red && (long long)k.G.Vh * c.tps / c.block + 1 <= a.red->nblocks_max) fit.push_back(c);
+        if (a.red && dslash_partial_cols(k.G.Vh, c) <= a.red->nblocks_max) fit.push_back(c);
       if (fit.empty()) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
       cands = fit;
     }
@@ -145,7 +154,7 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
     if (st) return st;
   }
   if (a.reduce != RED_NONE) {
-    int nbx = (int)(((long long)k.G.Vh * pick.tps + pick.block - 1) / pick.block);
+    const int nbx = dslash_partial_cols(k.G.Vh, pick);
     if (!a.red || nbx > a.red->nblocks_max)
       return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
     a.red->cols = nbx;  // row stride of the partials, for a FIN_DEFER consumer
@@ -257,19 +266,9 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
           cands.push_back(e);
         }
     std::string tkey = key;
-    if (a.reduce != RED_NONE) {
-      tkey += a.reduce == RED_DOT ? " red=dot" : " red=norm";
-      std::vector<TuneEntry> fit;   // every candidate must fit the reduction scratch
-      for (const TuneEntry& c : cands) {
-        MultiKArgs chk = a;
-        multi_tiles(chk, c.block, c.rhs_tile, c.tps);
-        bool ok = true;
-        for (int l = 0; l < a.nlat; ++l) ok &= (size_t)chk.lat[l].tiles_x <= a.pstride;
-        if (ok) fit.push_back(c);
-      }
-      if (fit.empty()) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
-      cands = fit;
-    }
+    // (a reduction launch stores one partial column per block; its grid is capped at the
+    // partials' row stride, so every candidate fits)
+    if (a.reduce != RED_NONE) tkey += a.reduce == RED_DOT ? " red=dot" : " red=norm";
     lq_status st = tune_pick(
         ctx, tkey, cands, s,
         [&](const TuneEntry& c) -> lq_status {
@@ -280,13 +279,7 @@ lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int rec
         &pick);
     if (st) return st;
   }
-  if (a.reduce != RED_NONE) {
-    MultiKArgs chk = a;
-    multi_tiles(chk, pick.block, pick.rhs_tile, pick.tps);
-    for (int l = 0; l < a.nlat; ++l)
-      if ((size_t)chk.lat[l].tiles_x > a.pstride)
-        return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
-  }
+  if (a.reduce != RED_NONE && a.pstride < 1) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "reduction scratch too small");
   cudaError_t e = fn(a, vp, pick.block, pick.rhs_tile, pick.tps, ctx->num_sms, s);
   if (e != cudaSuccess) return lq_cuda_fail(ctx, e, "k_dslash_multi");
   return LQ_OK;

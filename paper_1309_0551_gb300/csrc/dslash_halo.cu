@@ -44,13 +44,8 @@ __global__ void __launch_bounds__(128) k_dslash_halo(const HaloArgs a) {
   if (cb >= G.Vh) return;
   const int rhs = blockIdx.y;
   const size_t voff = (size_t)rhs * G.Vh, goff = (size_t)rhs * a.Vsh;
-  const int xh = cb % G.Lxh;
-  const int row = cb / G.Lxh;
-  const int y = row % G.Ly;
-  const int zt = row / G.Ly;
-  const int z = zt % G.Lz;
-  const int t = zt / G.Lz;
-  const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+  int xh, row, x, y, z, t;
+  cb_coords(G, cb, a.out_par, xh, row, x, y, z, t);
   const int opar = 1 - a.out_par;
   T acc[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll

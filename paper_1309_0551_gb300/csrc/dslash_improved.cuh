@@ -46,13 +46,8 @@ __global__ void __launch_bounds__(256) k_dslash_improved(const ImpKArgs a) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[r][k] = T(0);
   if (live) {
-    const int xh = cb % G.Lxh;
-    const int row = cb / G.Lxh;
-    const int y = row % G.Ly;
-    const int zt = row / G.Ly;
-    const int z = zt % G.Lz;
-    const int t = zt / G.Lz;
-    const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+    int xh, row, x, y, z, t;
+    cb_coords(G, cb, a.out_par, xh, row, x, y, z, t);
     const int opar = 1 - a.out_par;
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {

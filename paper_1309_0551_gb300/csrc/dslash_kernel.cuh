@@ -73,7 +73,7 @@ template <lq_prec GP, int R, lq_prec VP>
 static cudaError_t launch_dslash_shape(const DslashKArgs& k, int block, int tile, int tps, cudaStream_t s) {
   if (tps == kTpsRhsWarps) {
     if constexpr (GP != LQ_F64 && VP == LQ_F32) {
-      if (k.reduce != RED_NONE) return cudaErrorInvalidValue;
+      if (k.reduce != RED_NONE && k.red.finisher != FIN_DEFER) return cudaErrorInvalidValue;
       return launch_dslash_rw<GP, R>(k, block, tile, s);
     } else {
       return cudaErrorInvalidValue;

@@ -11,6 +11,7 @@
 #include "tune.cuh"
 
 constexpr int kMaxLat = 16;
+constexpr int kMaxRows = kMaxLat * 16;   // (lattice, rhs) systems of one launch
 enum { SKIP_INACTIVE = 1, SKIP_DONE = 2, SKIP_NO_RU = 3 };
 
 // A system is skipped when it is inactive (SKIP_INACTIVE), done (SKIP_DONE), or does not
@@ -39,14 +40,32 @@ struct MultiKArgs {
   size_t pstride;     // partials row stride (columns per (lattice, rhs) row)
   const CGScalars* skip_state;  // optional per-system state: tiles whose systems are all
   int skip_mode;                // skipped (system_skipped) are not computed
-  Reducer red;        // rows q = l * nrhs + rhs
+  Reducer red;        // rows q = l * nrhs + rhs; columns: the launch's blocks
+  int* cols_out;      // host: receives the launch's block count (partial columns per row)
   MLat lat[kMaxLat];
 };
+
+// Reductions of the persistent kernels: each block adds its tiles' sums per row in shared
+// memory (one writer per row: deterministic), then stores them as column blockIdx.x of
+// partials[row][pstride] for every row; unless the finisher is deferred (FIN_DEFER: a later
+// launch sums the rows), the last block sums the rows and runs the finisher.
+__device__ __forceinline__ void multi_rows_init(double* sRow, int nrows) {
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) sRow[i] = 0.0;
+  __syncthreads();
+}
+__device__ __forceinline__ void multi_rows_finish(const MultiKArgs& a, const double* sRow, int nrows) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) a.red.partials[(size_t)i * a.pstride + blockIdx.x] = sRow[i];
+  if (a.red.finisher != FIN_DEFER) grid_finish(a.red, nrows, a.pstride, [&](int) { return (int)gridDim.x; });
+}
 
 template <lq_prec GP, int R, lq_prec VP, int NR, int TPS>
 __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
   using T = typename LinkT<GP, R>::real;
   using VT = VecT<VP>;
+  __shared__ double sRow[kMaxRows];
+  const int nrows = a.nlat * a.nrhs;
+  if (a.reduce != RED_NONE) multi_rows_init(sRow, nrows);
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     int l = 0;
     while (l + 1 < a.nlat && tile >= a.lat[l + 1].tile0) ++l;
@@ -86,11 +105,10 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
     }
     if (a.reduce != RED_NONE) {
       const int nvalid = a.nrhs - rhs0 < NR ? a.nrhs - rhs0 : NR;
-      block_sum_store<NR>(part, a.red.partials + (size_t)(l * a.nrhs + rhs0) * a.pstride + tx, a.pstride, nvalid);
+      block_sum_add<NR>(part, sRow + l * a.nrhs + rhs0, nvalid);
     }
   }
-  if (a.reduce != RED_NONE)
-    grid_finish(a.red, a.nlat * a.nrhs, a.pstride, [&](int q) { return a.lat[q / a.nrhs].tiles_x; });
+  if (a.reduce != RED_NONE) multi_rows_finish(a, sRow, nrows);
 }
 
 // The multi-lattice form of the rhs-per-warp kernel (k_dslash_rw): a tile is (lattice,
@@ -105,9 +123,12 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a)
   using VT = VecT<LQ_F32>;
   __shared__ float2 sU[8][9][32];
   __shared__ int sN[8][32];
+  __shared__ double sRow[kMaxRows];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // 1-D block of 32 x RT threads
   constexpr int TR = RT * NRT;                // right-hand sides per tile
   const int nty = (a.nrhs + TR - 1) / TR;
+  const int nrows = a.nlat * a.nrhs;
+  if (a.reduce != RED_NONE) multi_rows_init(sRow, nrows);
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     int l = 0;
     while (l + 1 < a.nlat && tile >= a.lat[l + 1].tile0) ++l;
@@ -130,13 +151,8 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a)
     for (int r = 0; r < NRT; ++r) part[r] = 0.0;
     if (!skip) {
       const int cbc = cb < G.Vh ? cb : G.Vh - 1;
-      const int xh = cbc % G.Lxh;
-      const int row = cbc / G.Lxh;
-      const int y = row % G.Ly;
-      const int zt = row / G.Ly;
-      const int z = zt % G.Lz;
-      const int t = zt / G.Lz;
-      const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+      int xh, row, x, y, z, t;
+      cb_coords(G, cbc, a.out_par, xh, row, x, y, z, t);
       for (int h = w; h < 8; h += RT) {
         const int mu = h >> 1;
         const bool bwd = h & 1;
@@ -229,17 +245,16 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a)
       }
     }
     if (a.reduce != RED_NONE && rhs0 < a.nrhs) {
+      // the warp owning rows rhs0 .. rhs0 + NRT - 1 of this lattice in every tile adds its sums
 #pragma unroll
       for (int r = 0; r < NRT; ++r) {
         const double sum = warp_sum(part[r]);
-        if (lane == 0 && rhs0 + r < a.nrhs)
-          a.red.partials[(size_t)(l * a.nrhs + rhs0 + r) * a.pstride + tx] = sum;
+        if (lane == 0 && rhs0 + r < a.nrhs) sRow[l * a.nrhs + rhs0 + r] += sum;
       }
     }
     __syncthreads();   // shared memory is rewritten by the next tile
   }
-  if (a.reduce != RED_NONE)
-    grid_finish(a.red, a.nlat * a.nrhs, a.pstride, [&](int q) { return a.lat[q / a.nrhs].tiles_x; });
+  if (a.reduce != RED_NONE) multi_rows_finish(a, sRow, nrows);
 }
 
 // Launch-shape helpers -----------------------------------------------------------------
@@ -271,7 +286,9 @@ static cudaError_t launch_multi_rw_inst(MultiKArgs a, int num_sms, cudaStream_t 
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms * per_sm;
   if (grid > a.ntiles) grid = a.ntiles;
+  if (a.reduce != RED_NONE && (size_t)grid > a.pstride) grid = (int)a.pstride;
   if (grid < 1) return cudaSuccess;
+  if (a.cols_out) *a.cols_out = grid;
   k_dslash_multi_rw<GP, R, RT, NRT><<<grid, 32 * RT, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -302,7 +319,9 @@ static cudaError_t launch_multi_inst(MultiKArgs a, int block, int num_sms, cudaS
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms * per_sm;
   if (grid > a.ntiles) grid = a.ntiles;
+  if (a.reduce != RED_NONE && (size_t)grid > a.pstride) grid = (int)a.pstride;
   if (grid < 1) return cudaSuccess;
+  if (a.cols_out) *a.cols_out = grid;
   k_dslash_multi<GP, R, VP, NR, TPS><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }

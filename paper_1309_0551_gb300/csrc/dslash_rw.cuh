@@ -14,8 +14,13 @@
 // links to its right-hand sides.  Link loads and the 12-real reconstruction are done once
 // per site and hop, not once per rhs; each link element read from shared memory serves
 // NRT right-hand sides (in pairs, with packed FP32x2 FMAs, when NRT is even).
-// FP32 vectors and arithmetic; no fused reduction (RED_NONE).
-template <lq_prec GP, int R, int RT, int NRT>
+// FP32 vectors and arithmetic.  A fused reduction (RED_DOT / RED_NORM of the epilogue) is
+// stored, never finished here: every warp owns its right-hand sides, so it writes its
+// warp sum to partials[rhs][blockIdx.x] (gridDim.x columns per rhs) and a later launch
+// sums the rows (FIN_DEFER).  RED selects the instance with that reduction: the plain
+// operator is compiled without it (as a run-time branch it slowed the plain launches by a
+// quarter).
+template <lq_prec GP, int R, int RT, int NRT, bool RED>
 __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
   using L = LinkT<GP, R>;
   using VT = VecT<LQ_F32>;
@@ -25,13 +30,8 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
   const Geom& G = a.G;
   const int cb = blockIdx.x * 32 + lane;
   const int cbc = cb < G.Vh ? cb : G.Vh - 1;   // lanes past the end work on a valid site
-  const int xh = cbc % G.Lxh;
-  const int row = cbc / G.Lxh;
-  const int y = row % G.Ly;
-  const int zt = row / G.Ly;
-  const int z = zt % G.Lz;
-  const int t = zt / G.Lz;
-  const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+  int xh, row, x, y, z, t;
+  cb_coords(G, cbc, a.out_par, xh, row, x, y, z, t);
   pdl_wait();
   for (int h = w; h < 8; h += RT) {
     const int mu = h >> 1;
@@ -126,12 +126,18 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
       }
   }
   pdl_trigger();
-  if (cb < G.Vh) {
-    double part[NRT];
+  double part[NRT];
 #pragma unroll
-    for (int r = 0; r < NRT; ++r) part[r] = 0.0;
-    dslash_epilogue<LQ_F32, NRT, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED_NONE, a.rhs_stride, a.nrhs, rhs0,
-                                    cb, 0, part);
+  for (int r = 0; r < NRT; ++r) part[r] = 0.0;
+  if (cb < G.Vh)
+    dslash_epilogue<LQ_F32, NRT, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED ? a.reduce : RED_NONE, a.rhs_stride,
+                                    a.nrhs, rhs0, cb, 0, part);
+  if constexpr (RED) {
+#pragma unroll
+    for (int r = 0; r < NRT; ++r) {
+      const double sum = warp_sum(part[r]);
+      if (lane == 0 && rhs0 + r < a.nrhs) a.red.partials[(size_t)(rhs0 + r) * gridDim.x + blockIdx.x] = sum;
+    }
   }
 }
 
@@ -142,22 +148,28 @@ inline bool dslash_rw_shape_ok(int block, int tile) {
   return (rt == 2 || rt == 4 || rt == 8) && (nrt == 1 || nrt == 2 || nrt == 4) && rt * nrt <= 16;
 }
 
+template <lq_prec GP, int R, bool RED>
+static cudaError_t launch_dslash_rw_red(const DslashKArgs& k, int rt, int nrt, cudaStream_t s) {
+  dim3 grid((unsigned)((k.G.Vh + 31) / 32), (unsigned)((k.nrhs + rt * nrt - 1) / (rt * nrt)));
+  const bool pdl = k.pdl != 0;
+  switch (rt * 8 + nrt) {
+    case 2 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 2, 1, RED>, grid, dim3(64), 0, s, pdl, k);
+    case 2 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 2, 2, RED>, grid, dim3(64), 0, s, pdl, k);
+    case 2 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 2, 4, RED>, grid, dim3(64), 0, s, pdl, k);
+    case 4 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 4, 1, RED>, grid, dim3(128), 0, s, pdl, k);
+    case 4 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 4, 2, RED>, grid, dim3(128), 0, s, pdl, k);
+    case 4 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 4, 4, RED>, grid, dim3(128), 0, s, pdl, k);
+    case 8 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 8, 1, RED>, grid, dim3(256), 0, s, pdl, k);
+    case 8 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 8, 2, RED>, grid, dim3(256), 0, s, pdl, k);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <lq_prec GP, int R>
 static cudaError_t launch_dslash_rw(const DslashKArgs& k, int block, int tile, cudaStream_t s) {
   if (!dslash_rw_shape_ok(block, tile)) return cudaErrorInvalidValue;
   const int rt = block / 32, nrt = tile / rt;
-  dim3 grid((unsigned)((k.G.Vh + 31) / 32), (unsigned)((k.nrhs + tile - 1) / tile));
-  const bool pdl = k.pdl != 0;
-  switch (rt * 8 + nrt) {
-    case 2 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 2, 1>, grid, dim3(64), 0, s, pdl, k);
-    case 2 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 2, 2>, grid, dim3(64), 0, s, pdl, k);
-    case 2 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 2, 4>, grid, dim3(64), 0, s, pdl, k);
-    case 4 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 4, 1>, grid, dim3(128), 0, s, pdl, k);
-    case 4 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 4, 2>, grid, dim3(128), 0, s, pdl, k);
-    case 4 * 8 + 4: return launch_k(k_dslash_rw<GP, R, 4, 4>, grid, dim3(128), 0, s, pdl, k);
-    case 8 * 8 + 1: return launch_k(k_dslash_rw<GP, R, 8, 1>, grid, dim3(256), 0, s, pdl, k);
-    case 8 * 8 + 2: return launch_k(k_dslash_rw<GP, R, 8, 2>, grid, dim3(256), 0, s, pdl, k);
-    default: return cudaErrorInvalidValue;
-  }
+  if (k.reduce != RED_NONE) return launch_dslash_rw_red<GP, R, true>(k, rt, nrt, s);
+  return launch_dslash_rw_red<GP, R, false>(k, rt, nrt, s);
 }
 

@@ -52,13 +52,8 @@ __device__ __forceinline__ void dslash_hops(const char* __restrict__ gauge, size
   using L = LinkT<GP, R>;
   using VT = VecT<VP>;
   constexpr int DPT = 4 / TPS;   // directions per thread
-  const int xh = cb % G.Lxh;
-  const int row = cb / G.Lxh;    // y + Ly*(z + Lz*t)
-  const int y = row % G.Ly;
-  const int zt = row / G.Ly;
-  const int z = zt % G.Lz;
-  const int t = zt / G.Lz;
-  const int x = 2 * xh + ((y + z + t + out_par) & 1);
+  int xh, row, x, y, z, t;
+  cb_coords(G, cb, out_par, xh, row, x, y, z, t);
   const int opar = 1 - out_par;
   if constexpr (std::is_same<T, float>::value && NR % 2 == 0) {
     dslash_hops_pairs<GP, R, VP, NR, TPS>(gauge, blk_bytes, G, out_par, in, rhs_stride, nrhs, rhs0, cb, sub, x, y,

@@ -496,18 +496,60 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 }
 
 // Lattice geometry passed to kernels.
+// Division by an invariant divisor d >= 1 as a multiply-high, an add and two shifts, exact
+// for every 32-bit dividend (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994, in the add-and-shift form that needs no 33-bit multiplier):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, t = hi32(m n) and
+// n / d = (t + ((n - t) >> s1)) >> s2, s1 = min(l, 1), s2 = max(l - 1, 0).  The kernels'
+// site coordinates need three divisions per thread; as hardware-emulated division by a
+// run-time value they cost some 25 instructions each.
+struct FastDiv {
+  uint32_t m, s1, s2;
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
 struct Geom {
   int Lx, Ly, Lz, Lt;
   int Lxh;   // Lx / 2
   int Vh;    // sites per parity
   int S;     // plane length (padded Vh)
+  FastDiv dLxh, dLy, dLz;
 };
 
 inline Geom make_geom(const lq_gauge* g) {
   Geom G;
   G.Lx = g->dims[0]; G.Ly = g->dims[1]; G.Lz = g->dims[2]; G.Lt = g->dims[3];
   G.Lxh = G.Lx / 2; G.Vh = g->Vh; G.S = g->S;
+  G.dLxh = make_fastdiv(G.Lxh);
+  G.dLy = make_fastdiv(G.Ly);
+  G.dLz = make_fastdiv(G.Lz);
   return G;
+}
+
+// Coordinates of the site with checkerboard index cb on parity `par`:
+// cb = xh + Lxh * row, row = y + Ly * (z + Lz * t), x = 2 xh + ((y + z + t + par) & 1).
+__device__ __forceinline__ void cb_coords(const Geom& G, int cb, int par, int& xh, int& row, int& x, int& y,
+                                          int& z, int& t) {
+  row = (int)G.dLxh.div((uint32_t)cb);
+  xh = cb - row * G.Lxh;
+  const int zt = (int)G.dLy.div((uint32_t)row);
+  y = row - zt * G.Ly;
+  t = (int)G.dLz.div((uint32_t)zt);
+  z = zt - t * G.Lz;
+  x = 2 * xh + ((y + z + t + par) & 1);
 }
 
 // ------------------------------------------------------------------- internal API ------

@@ -277,6 +277,29 @@ __device__ __forceinline__ void block_sum_store(const double (&v)[NR], double* d
   __syncthreads();
 }
 
+// Block-wide sums of v[r] added to dst[r] for r < nvalid by one thread (every thread
+// calls; deterministic: a fixed tree per block, one writer).  Ends with a barrier.
+template <int NR>
+__device__ __forceinline__ void block_sum_add(const double (&v)[NR], double* dst, int nvalid) {
+  __shared__ double sm[NR][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    double x = warp_sum(v[r]);
+    if (lane == 0) sm[r][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double x = lane < nw ? sm[r][lane] : 0.0;
+      x = warp_sum(x);
+      if (lane == 0 && r < nvalid) dst[r] += x;
+    }
+  }
+  __syncthreads();
+}
+
 // End of a persistent kernel whose blocks stored per-row partials partials[q*stride + col]
 // (cols(q) columns for row q): the last block to finish sums each row in column order and
 // runs the finisher on it.  Every thread of every block calls this once.

@@ -175,13 +175,8 @@ __global__ void __launch_bounds__(256) k_wilson(const WilsonKArgs a) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= a.G.Vh) return;
   const Geom& G = a.G;
-  const int xh = cb % G.Lxh;
-  const int row = cb / G.Lxh;   // y + Ly*(z + Lz*t)
-  const int y = row % G.Ly;
-  const int zt = row / G.Ly;
-  const int z = zt % G.Lz;
-  const int t = zt / G.Lz;
-  const int x = 2 * xh + ((y + z + t + a.out_par) & 1);
+  int xh, row, x, y, z, t;   // row = y + Ly*(z + Lz*t)
+  cb_coords(G, cb, a.out_par, xh, row, x, y, z, t);
   const size_t rbase = (size_t)blockIdx.y * a.rhs_stride;
   // neighbours on the other parity
   const int xf = (x + 1 == G.Lx) ? 0 : x + 1;
