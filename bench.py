@@ -430,7 +430,10 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
         torch.cuda.empty_cache()
     if want("lone"):
         # one stream: each half Dslash waits for the previous one (the way a solver issues
-        # them), so a launch's ramp-up and tail are not hidden by other launches in flight
+        # them), so a launch's ramp-up and tail are not hidden by other launches in flight;
+        # shapes tuned for lone launches (a context of its own, tuning mode 1)
+        lctx = lq.Context(torch.cuda.current_device())
+        lctx.set_tuning(1)
         for prec, recon, vec, dims in (("f32", 18, "f32", DIMS), ("bf16", 12, "bf16", DIMS),
                                        ("f32", 12, "f32", (32, 32, 32, 32)),
                                        ("bf16", 12, "bf16", (32, 32, 32, 32))):
@@ -439,19 +442,21 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
                 synth.gauge_field(dims, "near_identity", seed=3, eps=0.3)).cuda()
             sb = site_bytes(prec, recon, vec)
             K = ring_size(Vhl * sb, l2, 1)
-            gauges, ins, ts, outs = make_ring(lq, ctx, Ul, dims, prec, recon, vec, K)
+            gauges, ins, ts, outs = make_ring(lq, lctx, Ul, dims, prec, recon, vec, K)
             vc = lq.PREC[vec]
-            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), 1)
+            g = GraphStep(torch, lambda ss: run_step(lq, lctx, gauges, ins, ts, outs, vc, ss, 20), 1)
             ms, launches, _ = time_steps(torch, g, 10, 3, stream)
             del g
             us = ms * 1000.0 / launches
             gbs = Vhl * sb / us / 1e3
+            dkey = f"g={prec}/{recon} v={vec} dims={'x'.join(map(str, dims))} nrhs=1"
             out[f"lone/{prec}/{recon}/{vec}/{'x'.join(map(str, dims))}"] = {
                 "gflops": round(Vhl * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
                 "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K,
-                "streams": 1}
+                "streams": 1, "launch_shape": [l for l in lctx.tune_report().splitlines() if dkey in l]}
             del gauges, ins, ts, outs, Ul
             torch.cuda.empty_cache()
+        del lctx
     if want("improved"):
         # improved staggered Dslash: fat one-hop + Naik three-hop links (16 hops, 1146 flops)
         for prec in ("f32", "bf16"):

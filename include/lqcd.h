@@ -77,12 +77,14 @@ const char* lq_last_error(const lq_context* ctx);
 const char* lq_status_string(lq_status s);
 /* Synchronise `stream`, then report and clear the context's device status word: the
  * flags that bounded device waits set when they gave up since the last lq_sync.  Such a
- * wait exists in the batched SU(3) kernels (su3_*_batch), where one thread per block
- * waits, at most ~2^24 polls, for the TMA bulk copies that bring the block's operand slice
+ * wait exists in the batched SU(3) kernels (su3_*_batch) and in the link-staging half
+ * Dslash (dslash_eo and the solvers, when the tuner picks it), where one thread per block
+ * waits, at most ~2^24 polls, for the TMA bulk copies that bring the block's operand slices
  * into shared memory; if they do not arrive, the block records the failure, waits once
  * more (bounded) so that it does not leave with copies in flight, and skips its work.
  * Those entry points are asynchronous and return LQ_OK at launch, so their outputs can
- * only be trusted after an lq_sync that returns LQ_OK.
+ * only be trusted after an lq_sync that returns LQ_OK (the CG solvers check the word
+ * themselves).
  * Returns LQ_ERR_TIMEOUT if any wait gave up (outputs of the calls issued on this context
  * since the last lq_sync may be unwritten), LQ_ERR_CUDA for an error of the stream, LQ_OK
  * otherwise. */
@@ -336,7 +338,8 @@ typedef struct {
  *   stats: host array of nrhs entries (may be NULL).
  * Synchronises `stream` at each check (every check_every iterations).  Returns
  * LQ_ERR_NOT_CONVERGED if maxiter was reached (stats filled in), LQ_ERR_NUMERIC if b or a
- * residual holds NaN/Inf. */
+ * residual holds NaN/Inf, LQ_ERR_TIMEOUT if the context's device status word holds a
+ * bounded wait that gave up (see lq_sync; the word is then cleared). */
 lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_gauge* U_lo, double mass,
                    const void* b, void* x, int nrhs, const lq_cg_params* params,
                    lq_cg_stats* stats, lq_stream stream);

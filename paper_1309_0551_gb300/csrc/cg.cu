@@ -710,6 +710,19 @@ lq_status read_result(Solver& S, std::vector<double>& out, int rows = 0) {
   return LQ_OK;
 }
 
+// After a solve: a bounded device wait that gave up since the context's status word was
+// last reported (during the solve: the link-staging Dslash, whose block then skipped its
+// work) invalidates the result: report LQ_ERR_TIMEOUT and clear the flag.
+lq_status solve_status(lq_context* ctx, cudaStream_t s) {
+  unsigned int flags = 0;
+  LQ_CUDA(ctx, cudaMemcpyAsync(&flags, ctx->dev_status, sizeof flags, cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(ctx, cudaStreamSynchronize(s));
+  if (!flags) return LQ_OK;
+  LQ_CUDA(ctx, cudaMemsetAsync(ctx->dev_status, 0, sizeof flags, s));
+  return lq_fail(ctx, LQ_ERR_TIMEOUT, "a bounded device wait gave up (status flags 0x%x) during the solve or "
+                                      "before it, unreported: the solution is not valid", flags);
+}
+
 lq_status work_stream(lq_context* ctx, cudaStream_t* out) {
   static thread_local cudaStream_t cache[64] = {};
   int dev = ctx->device;
@@ -1005,6 +1018,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   LQ_CUDA(ctx, cudaMemsetAsync(S.counter, 0, sizeof(unsigned int), S.s));
   int converged = 0;
   st = run_solver(S, *params, stats, &converged);
+  if (!st) st = solve_status(ctx, S.s);
   cudaEventRecord(ev, S.s);
   cudaStreamWaitEvent(user, ev, 0);
   cudaEventDestroy(ev);
@@ -1128,6 +1142,7 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   int converged = 0;
   st = run_solver(S, *params, stats, &converged, /*use_graph=*/false);
   ctx->tuning = tuning;
+  if (!st) st = solve_status(ctx, S.s);
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
     for (int i = 0; i < nrhs; ++i) stats[i].seconds = secs;
@@ -1262,6 +1277,7 @@ extern "C" lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge*
                                  cudaMemcpyDeviceToDevice, S.s));
   int converged = 0;
   st = run_solver(S, *params, stats, &converged);
+  if (!st) st = solve_status(ctx, S.s);
   if (!st)
     for (int l = 0; l < nlat && !st; ++l) {
       cudaError_t e = cudaMemcpyAsync(x[l], (const char*)S.x + B.voff[l] * 48, (size_t)nrhs * U_hi[l]->Vh * 48,

@@ -33,6 +33,17 @@ static DslashLaunchFn pick_fn(const lq_gauge* g) {
   return nullptr;
 }
 
+// Sites per block of the link-staging kernel k_dslash_tma for this gauge (0: not used).
+static int tma_block(const lq_gauge* g) {
+  const Geom G = make_geom(g);
+  switch (g->prec) {
+    case LQ_F32: return dslash_tma_fn_f32(g->recon)(G);
+    case LQ_BF16: return dslash_tma_fn_bf16(g->recon)(G);
+    case LQ_F16: return dslash_tma_fn_f16(g->recon)(G);
+    default: return 0;
+  }
+}
+
 bool dslash_vec_ok(lq_prec gauge, lq_prec vec) {
   if (gauge == LQ_F64) return vec == LQ_F64;
   return vec == LQ_F32 || vec == LQ_BF16 || vec == LQ_F16;
@@ -73,6 +84,7 @@ static std::vector<TuneEntry> dslash_candidates(lq_prec gp, int nrhs) {
 // blocks (32 sites per block for the rhs-per-warp kernel).
 static int dslash_partial_cols(int Vh, const TuneEntry& c) {
   if (c.tps == kTpsRhsWarps) return (Vh + 31) / 32;
+  if (c.tps == kTpsTma) return (Vh + c.block - 1) / c.block;
   return (int)(((long long)Vh * c.tps + c.block - 1) / c.block);
 }
 
@@ -93,6 +105,7 @@ static DslashKArgs make_kargs(const DslashArgs& a) {
   if (a.red) k.red = *a.red;
   else k.red = Reducer{nullptr, nullptr, nullptr, 0, 0, nullptr};
   k.pdl = a.pdl ? 1 : 0;
+  k.status = nullptr;
   return k;
 }
 
@@ -100,6 +113,7 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   DslashLaunchFn fn = pick_fn(a.U);
   if (!fn) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "bad gauge precision");
   DslashKArgs k = make_kargs(a);
+  k.status = ctx->dev_status;
   // Tuning launches must be repeatable.  A launch without reduction is tuned on the plain
   // operator; a launch with a reduction is tuned as itself (its cost depends on the number
   // of blocks it reduces over), which is repeatable because the solvers never let out alias
@@ -118,11 +132,15 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   const TuneEntry& f = ctx->forced;
   // the rhs-per-warp kernel: FP32 vectors, two or more rhs, a fused reduction only as
   // deferred per-block partials (FIN_DEFER)
-  const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.nrhs >= 2 &&
-                     (a.reduce == RED_NONE || (a.red && a.red->finisher == FIN_DEFER));
+  const bool defer_ok = a.reduce == RED_NONE || (a.red && a.red->finisher == FIN_DEFER);
+  const bool rw_ok = a.vec_prec == LQ_F32 && a.U->prec != LQ_F64 && a.nrhs >= 2 && defer_ok;
+  // the link-staging kernel: a geometry of whole x-rows per block (tma_block)
+  const int tmaT = defer_ok ? tma_block(a.U) : 0;
   if (f.block && dslash_shape_ok(f.rhs_tile, f.tps) && f.rhs_tile <= a.nrhs &&
-      !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && dslash_rw_shape_ok(f.block, f.rhs_tile)))) {
+      !(a.U->prec == LQ_F64 && f.rhs_tile > 4) && (f.tps != kTpsRhsWarps || (rw_ok && dslash_rw_shape_ok(f.block, f.rhs_tile))) &&
+      (f.tps != kTpsTma || tmaT > 0)) {
     pick = f;
+    if (f.tps == kTpsTma) pick.block = tmaT;
   } else {
     std::string key = dslash_key(a.U, a.vec_prec, a.nrhs);
     std::vector<TuneEntry> cands = dslash_candidates(a.U->prec, a.nrhs);
@@ -135,6 +153,11 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
           e.block = 32 * rt; e.rhs_tile = t; e.tps = kTpsRhsWarps;
           cands.push_back(e);
         }
+    if (tmaT > 0) {
+      TuneEntry e;
+      e.block = tmaT; e.rhs_tile = 1; e.tps = kTpsTma;
+      cands.push_back(e);
+    }
     if (a.reduce != RED_NONE) {
       key += a.reduce == RED_DOT ? " red=dot" : " red=norm";
       std::vector<TuneEntry> fit;  // every candidate must fit the reduction scratch
@@ -189,6 +212,11 @@ extern "C" lq_status dslash_eo(lq_context* ctx, const lq_gauge* U, const void* i
   a.nrhs = nrhs;
   a.vec_prec = vec_prec;
   a.rhs_stride = U->Vh;
+  // Programmatic dependent launch: the kernel's blocks may be scheduled while the previous
+  // kernel on the stream drains; they wait (griddepcontrol.wait) before touching memory,
+  // and a predecessor that never triggers early is simply waited for.  Hides the launch
+  // and ramp-up of a chain of half Dslash calls.
+  a.pdl = true;
   return launch_dslash(ctx, a, (cudaStream_t)stream);
 }
 

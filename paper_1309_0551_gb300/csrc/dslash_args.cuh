@@ -20,4 +20,5 @@ struct DslashKArgs {
   int reduce;
   Reducer red;
   int pdl;     // host side only: launch with programmatic dependent launch
+  unsigned int* status;   // the context's device status word (bounded waits that gave up)
 };

@@ -10,3 +10,7 @@ DslashLaunchFn dslash_fn_bf16(int recon) {
 MultiLaunchFn dslash_multi_fn_bf16(int recon) {
   return recon == 12 ? multi_launch_gauge<LQ_BF16, 12> : multi_launch_gauge<LQ_BF16, 18>;
 }
+
+DslashTmaBlockFn dslash_tma_fn_bf16(int recon) {
+  return recon == 12 ? dslash_tma_block_of<LQ_BF16, 12> : dslash_tma_block_of<LQ_BF16, 18>;
+}

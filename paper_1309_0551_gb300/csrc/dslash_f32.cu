@@ -10,3 +10,7 @@ DslashLaunchFn dslash_fn_f32(int recon) {
 MultiLaunchFn dslash_multi_fn_f32(int recon) {
   return recon == 12 ? multi_launch_gauge<LQ_F32, 12> : multi_launch_gauge<LQ_F32, 18>;
 }
+
+DslashTmaBlockFn dslash_tma_fn_f32(int recon) {
+  return recon == 12 ? dslash_tma_block_of<LQ_F32, 12> : dslash_tma_block_of<LQ_F32, 18>;
+}

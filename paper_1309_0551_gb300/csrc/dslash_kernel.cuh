@@ -9,6 +9,7 @@
 #include "dslash_args.cuh"
 #include "dslash_rw.cuh"
 #include "dslash_site.cuh"
+#include "dslash_tma.cuh"
 #include "lqcd_internal.cuh"
 #include "tune.cuh"
 
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
 // dslash_shape_ok() (and dslash_rw_shape_ok()) tell the tuner.
 inline bool dslash_shape_ok(int tile, int tps) {
   if (tps == kTpsRhsWarps) return tile >= 2 && tile <= 16;   // with the block: dslash_rw_shape_ok
+  if (tps == kTpsTma) return tile == 1;                        // block from the geometry
   if (tile == 1 || tile == 2) return tps == 1 || tps == 2 || tps == 4;
   if (tile == 4) return tps == 1 || tps == 2;
   return tile == 8 && tps == 1;
@@ -71,6 +73,7 @@ static cudaError_t launch_dslash_inst(const DslashKArgs& k, int block, cudaStrea
 
 template <lq_prec GP, int R, lq_prec VP>
 static cudaError_t launch_dslash_shape(const DslashKArgs& k, int block, int tile, int tps, cudaStream_t s) {
+  if (tps == kTpsTma) return launch_dslash_tma<GP, R, VP>(k, s);
   if (tps == kTpsRhsWarps) {
     if constexpr (GP != LQ_F64 && VP == LQ_F32) {
       if (k.reduce != RED_NONE && k.red.finisher != FIN_DEFER) return cudaErrorInvalidValue;
@@ -112,7 +115,15 @@ cudaError_t dslash_launch_gauge(const DslashKArgs& k, lq_prec vp, int block, int
   }
 }
 
+// Sites per block of the link-staging kernel for a gauge (0: not applicable).
+template <lq_prec GP, int R>
+int dslash_tma_block_of(const Geom& G) { return dslash_tma_block<GP, R>(G); }
+using DslashTmaBlockFn = int (*)(const Geom&);
+
 // Defined in the per-precision translation units.
+DslashTmaBlockFn dslash_tma_fn_f32(int recon);
+DslashTmaBlockFn dslash_tma_fn_bf16(int recon);
+DslashTmaBlockFn dslash_tma_fn_f16(int recon);
 DslashLaunchFn dslash_fn_f64(int recon);
 DslashLaunchFn dslash_fn_f32(int recon);
 DslashLaunchFn dslash_fn_bf16(int recon);

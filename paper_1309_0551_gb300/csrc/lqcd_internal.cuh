@@ -25,6 +25,9 @@ struct TuneEntry {
 // TuneEntry::tps value that selects the multi-RHS Dslash with one thread per (site, rhs):
 // blocks of 32 sites x rhs_tile warps, links shared through shared memory (k_dslash_rw).
 constexpr int kTpsRhsWarps = 8;
+// TuneEntry::tps value that selects the link-staging kernel k_dslash_tma (one thread per
+// site, blocks of whole x-rows, links brought into shared memory by TMA bulk copies).
+constexpr int kTpsTma = 16;
 
 // Flags of the context's device status word (lq_context::dev_status), set by kernels
 // whose bounded waits gave up; lq_sync reports and clears them.
@@ -99,6 +102,9 @@ lq_status lq_check_dims(lq_context* ctx, const int dims[4]);
 
 template <class T> struct Cplx { T re, im; };
 
+// A plain load (generic address: global or shared memory), where __ldg needs global.
+template <class T> __device__ __forceinline__ T ld_plain(const T* p) { return *p; }
+
 // Link storage: the 18 (or 12) reals of a link, row-major complex (re, im), are split
 // into planes; plane k of a (direction, parity) block is an array of S chunks, one chunk
 // per site in checkerboard order.  All chunks of a plane have the same width (16, 8 or
@@ -106,7 +112,8 @@ template <class T> struct Cplx { T re, im; };
 template <lq_prec P, int R> struct LinkT;
 
 // Each format offers load_raw() (the stored chunks, undecoded: issued early, cheap to
-// hold), decode() (to reals) and load() = decode(load_raw()).
+// hold), decode() (to reals) and load() = decode(load_raw()); load_raw_plain() reads the
+// same plane layout through a generic pointer (a block's copy in shared memory).
 template <int R> struct LinkT<LQ_F64, R> {
   using real = double;
   static constexpr int NREAL = R;
@@ -117,6 +124,13 @@ template <int R> struct LinkT<LQ_F64, R> {
     const double2* p = reinterpret_cast<const double2*>(blk);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) w.c[k] = __ldg(p + (size_t)k * S + cb);
+    return w;
+  }
+  __device__ __forceinline__ static Raw load_raw_plain(const char* blk, int S, int cb) {
+    Raw w;
+    const double2* p = reinterpret_cast<const double2*>(blk);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) w.c[k] = ld_plain(p + (size_t)k * S + cb);
     return w;
   }
   __device__ __forceinline__ static void decode(const Raw& w, double* u) {
@@ -144,6 +158,14 @@ template <> struct LinkT<LQ_F32, 18> {
 #pragma unroll
     for (int k = 0; k < 4; ++k) w.a[k] = __ldg(p4 + (size_t)k * S + cb);
     w.b = __ldg(reinterpret_cast<const float2*>(blk + (size_t)S * 64) + cb);
+    return w;
+  }
+  __device__ __forceinline__ static Raw load_raw_plain(const char* blk, int S, int cb) {
+    Raw w;
+    const float4* p4 = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w.a[k] = ld_plain(p4 + (size_t)k * S + cb);
+    w.b = ld_plain(reinterpret_cast<const float2*>(blk + (size_t)S * 64) + cb);
     return w;
   }
   __device__ __forceinline__ static void decode(const Raw& w, float* u) {
@@ -177,6 +199,13 @@ template <> struct LinkT<LQ_F32, 12> {
     const float4* p4 = reinterpret_cast<const float4*>(blk);
 #pragma unroll
     for (int k = 0; k < 3; ++k) w.a[k] = __ldg(p4 + (size_t)k * S + cb);
+    return w;
+  }
+  __device__ __forceinline__ static Raw load_raw_plain(const char* blk, int S, int cb) {
+    Raw w;
+    const float4* p4 = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w.a[k] = ld_plain(p4 + (size_t)k * S + cb);
     return w;
   }
   __device__ __forceinline__ static void decode(const Raw& w, float* u) {
@@ -245,6 +274,14 @@ template <lq_prec P> struct Link16<P, 18> {
     w.b = __ldg(reinterpret_cast<const uint32_t*>(blk + (size_t)S * 32) + cb);
     return w;
   }
+  __device__ __forceinline__ static Raw load_raw_plain(const char* blk, int S, int cb) {
+    Raw w;
+    const uint4* p = reinterpret_cast<const uint4*>(blk);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) w.a[k] = ld_plain(p + (size_t)k * S + cb);
+    w.b = ld_plain(reinterpret_cast<const uint32_t*>(blk + (size_t)S * 32) + cb);
+    return w;
+  }
   __device__ __forceinline__ static void decode(const Raw& w, float* u) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -281,6 +318,12 @@ template <lq_prec P> struct Link16<P, 12> {
     Raw w;
     w.a = __ldg(reinterpret_cast<const uint4*>(blk) + cb);
     w.b = __ldg(reinterpret_cast<const uint2*>(blk + (size_t)S * 16) + cb);
+    return w;
+  }
+  __device__ __forceinline__ static Raw load_raw_plain(const char* blk, int S, int cb) {
+    Raw w;
+    w.a = ld_plain(reinterpret_cast<const uint4*>(blk) + cb);
+    w.b = ld_plain(reinterpret_cast<const uint2*>(blk + (size_t)S * 16) + cb);
     return w;
   }
   __device__ __forceinline__ static void decode(const Raw& w, float* u) {
