@@ -11,11 +11,16 @@
 //                Lt - 1).
 // Placed in shared memory so that every hop but the backward x one reads its link at the
 // thread's own index, each run is one cp.async.bulk per storage plane: one warp issues all
-// of them at block start, so the block's 8 T links are in flight at once -- what a lone
-// launch on a small lattice lacks, with a few blocks per SM and one load chain per thread.
-// The neighbour vectors (4-8% of the bytes) come through L1/L2 as in k_dslash.  The wait
-// for the copies is bounded (tma.cuh): on expiry the block records kDevTmaTimeout in the
-// status word, waits once more and skips its work (lq_sync reports it).
+// of them at block start, so the block's 8 T links are in flight at once (what a lone
+// launch on a small lattice lacks: a few blocks per SM, one load chain per thread), each
+// hop on its own mbarrier so that the arithmetic starts when hop 0 has landed.  The
+// neighbour vectors (4-8% of the bytes) come through L1/L2 as in k_dslash, issued before
+// the waits.  Every wait is bounded (tma.cuh): on expiry the thread records kDevTmaTimeout
+// in the status word, waits once more for the remaining hops and stores nothing.
+// Measured on GB300 it runs slower than k_dslash in every regime timed (16^3 x 32 and 32^4,
+// one launch at a time or four in flight): it holds 12-24 warps per SM where k_dslash
+// holds up to 40, and k_dslash's coalesced loads already bring the links at the copy
+// bandwidth.  It stays a tuner candidate, picked only where it is the fastest.
 // FP32 arithmetic (links of FP32, BF16 or FP16 storage, vectors of the same precisions),
 // one thread per site, the block's right-hand sides one after another over the staged
 // links; a fused reduction is stored as per-block partials (FIN_DEFER).
@@ -39,7 +44,7 @@ template <lq_prec P, int R> struct TmaPlanes {
 };
 
 // Sites per block for this geometry and link size, or 0 when the kernel does not apply:
-// T = nr * Lx/2 with nr | Ly, T a multiple of 32 in [64, 256], 8 T links within
+// the largest T = nr * Lx/2 with nr | Ly, T a multiple of 32 in [64, 256], 8 T links within
 // kTmaMaxSmem; runs start at multiples of Lx/2, so 8-byte planes need Lx/2 even and
 // 4-byte planes Lx/2 a multiple of 4 (16-byte aligned copies).
 inline int dslash_tma_sites(const Geom& G, size_t link_bytes, int min_chunk) {
@@ -49,7 +54,7 @@ inline int dslash_tma_sites(const Geom& G, size_t link_bytes, int min_chunk) {
     if (G.Ly % nr) continue;
     const int T = nr * G.Lxh;
     if (T % 32 || T < 64 || T > 256 || 8 * (size_t)T * link_bytes > kTmaMaxSmem) continue;
-    best = T;   // the largest that fits
+    best = T;   // the largest: fewer, larger copies (runs of 64 sites, 0.5-1 KB, ran slower)
   }
   return best;
 }
@@ -96,49 +101,10 @@ __global__ void __launch_bounds__(256) k_dslash_tma(const DslashKArgs a, int T) 
   using PL = TmaPlanes<GP, R>;
   constexpr int kLink = (int)L::bytes_per_site;
   extern __shared__ __align__(128) unsigned char sm[];   // [hop][plane][T chunks]
-  __shared__ uint64_t bar;
-  __shared__ int ok;
+  __shared__ uint64_t bar[8];                              // one per hop: compute starts with hop 0
   const Geom& G = a.G;
   const int c0 = blockIdx.x * T;
   const int i = threadIdx.x;
-  pdl_wait();   // the links may be written by the previous kernel (a re-pack)
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) {
-      tma::mbar_init(&bar, 1);
-      tma::mbar_expect_tx(&bar, (uint32_t)(8 * T * kLink));
-    }
-    __syncwarp();
-    // the warp's lanes share out the (hop, run, plane) copies
-    int item = 0;
-#pragma unroll 1
-    for (int h = 0; h < 8; ++h) {
-      TmaRun runs[2];
-      const int nr = tma_hop_runs(G, h, c0, T, runs);
-      const int mu = h >> 1;
-      const char* blk = a.gauge + (size_t)(2 * mu + ((h & 1) ? 1 - a.out_par : a.out_par)) * a.blk_bytes;
-      unsigned char* hs = sm + (size_t)h * T * kLink;
-      int pre = 0;   // bytes of the planes before plane k, per site
-#pragma unroll
-      for (int k = 0; k < PL::n; ++k) {
-        const int ch = PL::chunk(k);
-        for (int q = 0; q < nr; ++q, ++item) {
-          if ((item & 31) != (int)threadIdx.x) continue;
-          tma::load(hs + (size_t)T * pre + (size_t)runs[q].dst * ch, blk + (size_t)G.S * pre + (size_t)runs[q].src * ch,
-                    (uint32_t)(runs[q].n * ch), &bar);
-        }
-        pre += ch;
-      }
-    }
-    if (threadIdx.x == 0) {
-      ok = tma::mbar_wait(&bar, 0);
-      if (!ok) {
-        atomicOr(a.status, kDevTmaTimeout);
-        tma::mbar_wait(&bar, 0);
-      }
-    }
-  }
-  __syncthreads();
-  if (!ok) return;
   const int cb = c0 + i;   // < Vh: T divides Vh
   int xh, row, x, y, z, t;
   cb_coords(G, cb, a.out_par, xh, row, x, y, z, t);
@@ -157,17 +123,55 @@ __global__ void __launch_bounds__(256) k_dslash_tma(const DslashKArgs a, int T) 
     sg[2 * mu] = eta;
     sg[2 * mu + 1] = -eta;
   }
+  pdl_wait();   // the links and the input may be written by the previous kernel
+  if (threadIdx.x < 32) {
+    if (threadIdx.x < 8) {
+      tma::mbar_init(&bar[threadIdx.x], 1);
+      tma::mbar_expect_tx(&bar[threadIdx.x], (uint32_t)(T * kLink));
+    }
+    __syncwarp();
+    // the warp's lanes share out the (hop, run, plane) copies, hop 0 first
+    int item = 0;
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+      TmaRun runs[2];
+      const int nr = tma_hop_runs(G, h, c0, T, runs);
+      const int mu = h >> 1;
+      const char* blk = a.gauge + (size_t)(2 * mu + ((h & 1) ? 1 - a.out_par : a.out_par)) * a.blk_bytes;
+      unsigned char* hs = sm + (size_t)h * T * kLink;
+      int pre = 0;   // bytes of the planes before plane k, per site
+#pragma unroll
+      for (int k = 0; k < PL::n; ++k) {
+        const int ch = PL::chunk(k);
+        for (int q = 0; q < nr; ++q, ++item) {
+          if ((item & 31) != (int)threadIdx.x) continue;
+          tma::load(hs + (size_t)T * pre + (size_t)runs[q].dst * ch, blk + (size_t)G.S * pre + (size_t)runs[q].src * ch,
+                    (uint32_t)(runs[q].n * ch), &bar[h]);
+        }
+        pre += ch;
+      }
+    }
+  }
+  __syncthreads();   // the barriers are initialised before anyone waits on them
+  bool ok = true;
   for (int rhs = 0; rhs < a.nrhs; ++rhs) {
     const size_t voff = (size_t)rhs * a.rhs_stride;
+    float v[8][6];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) VT::load(a.in, voff + nb[h], v[h]);   // in flight with the links
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 8; ++h) {
-      float u[18], v[6];
-      VT::load(a.in, voff + nb[h], v);
+      if (rhs == 0 && ok && !tma::mbar_wait(&bar[h], 0)) {
+        ok = false;
+        atomicOr(a.status, kDevTmaTimeout);
+        for (int g = h; g < 8; ++g) tma::mbar_wait(&bar[g], 0);   // once more, bounded
+      }
+      float u[18];
       L::decode(L::load_raw_plain(reinterpret_cast<const char*>(sm + (size_t)h * T * kLink), T, lidx[h]), u);
       if (R == 12) reconstruct_row2(u);
-      if (h & 1) adj_mat_vec_acc(u, v, acc, sg[h]);
-      else mat_vec_acc(u, v, acc, sg[h]);
+      if (h & 1) adj_mat_vec_acc(u, v[h], acc, sg[h]);
+      else mat_vec_acc(u, v[h], acc, sg[h]);
     }
     float res[6];
     double part[1] = {0.0};
@@ -185,13 +189,13 @@ __global__ void __launch_bounds__(256) k_dslash_tma(const DslashKArgs a, int T) 
 #pragma unroll
       for (int k = 0; k < 6; ++k) res[k] = fmaf((float)a.a2, w2v[k], res[k]);
     }
-    VT::store(a.out, voff + cb, res);
+    if (ok) VT::store(a.out, voff + cb, res);   // a block whose links did not arrive writes nothing
     if constexpr (RED) {
       // the site's share in the working precision (six products), summed over sites in FP64
       float ps = 0.f;
 #pragma unroll
       for (int k = 0; k < 6; ++k) ps = fmaf(a.reduce == RED_DOT ? w[k] : res[k], res[k], ps);
-      part[0] = (double)ps;
+      part[0] = ok ? (double)ps : 0.0;
       block_sum_store<1>(part, a.red.partials + (size_t)rhs * gridDim.x + blockIdx.x, 1, 1);
     }
   }
