@@ -527,35 +527,51 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             del wg, wins, wtmp, wout
             torch.cuda.empty_cache()
     if want("multi_rhs"):
-        # multi-RHS Dslash (links loaded once per site for all right-hand sides)
-        for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
-            sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
-            K = ring_size(Vh * sb, l2, nstreams)
-            gauges = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
-            chi = torch.from_numpy(synth.fermion_field(DIMS, nrhs, seed=12)).to(torch.complex64)
-            ins = [chi.cuda() for _ in range(K)]
-            ts = [torch.empty_like(ins[0]) for _ in range(K)]
-            outs = [torch.empty_like(ins[0]) for _ in range(K)]
+        # multi-RHS Dslash (links loaded once per site for all right-hand sides): canonical
+        # [rhs][site][3] vectors through dslash_eo, and the paired colour-planar layout
+        # through dslash_eo_paired (converted once, outside the timed region)
+        for layout in ("canonical", "paired"):
+            for prec, recon, nrhs in (("f32", 12, 8), ("f32", 18, 8), ("bf16", 12, 8), ("f32", 12, 16)):
+                sb = 8 * recon * BYTES[prec] + nrhs * 12 * BYTES["f32"]
+                K = ring_size(Vh * sb, l2, nstreams)
+                gauges = [lq.lq_gauge_pack(ctx, DIMS, U_dev, prec, recon) for _ in range(K)]
+                chi = torch.from_numpy(synth.fermion_field(DIMS, nrhs, seed=12)).to(torch.complex64).cuda()
+                if layout == "paired":
+                    pchi = torch.empty(lq.paired_numel(Vh, nrhs), dtype=torch.float32, device="cuda")
+                    lq.lq_vec_pair(ctx, Vh, nrhs, chi, pchi)
+                    ins = [pchi.clone() for _ in range(K)]
+                    del pchi
+                else:
+                    ins = [chi.clone() for _ in range(K)]
+                del chi
+                ts = [torch.empty_like(ins[0]) for _ in range(K)]
+                outs = [torch.empty_like(ins[0]) for _ in range(K)]
 
-            def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs):
-                h = 0
-                for a in range(10):
-                    s_ = ss[a % len(ss)]
-                    c, c2 = h % K, (h + 1) % K
-                    lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
-                    lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
-                    h += 2
-                return 20
-            g = GraphStep(torch, mstep, nstreams)
-            ms, launches, _ = time_steps(torch, g, 10, 3, stream)
-            del g
-            us = ms * 1000.0 / launches
-            gbs = Vh * sb / us / 1e3
-            out[f"multi_rhs/{prec}/{recon}/nrhs{nrhs}"] = {
-                "gflops": round(Vh * nrhs * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
-                "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
-            del gauges, ins, ts, outs
-            torch.cuda.empty_cache()
+                def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs, layout=layout):
+                    h = 0
+                    for a in range(10):
+                        s_ = ss[a % len(ss)]
+                        c, c2 = h % K, (h + 1) % K
+                        if layout == "paired":
+                            lq.dslash_eo_paired(ctx, gauges[c], ins[c], ts[c], 1, nrhs, s_)
+                            lq.dslash_eo_paired(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, s_)
+                        else:
+                            lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
+                            lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
+                        h += 2
+                    return 20
+                g = GraphStep(torch, mstep, nstreams)
+                ms, launches, _ = time_steps(torch, g, 10, 3, stream)
+                del g
+                us = ms * 1000.0 / launches
+                gbs = Vh * sb / us / 1e3
+                name = "multi_rhs" if layout == "canonical" else "multi_rhs_paired"
+                out[f"{name}/{prec}/{recon}/nrhs{nrhs}"] = {
+                    "gflops": round(Vh * nrhs * FLOPS_PER_SITE / us / 1e3, 1), "gbs": round(gbs, 1),
+                    "frac": round(gbs / peak, 3), "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K,
+                    "layout": layout}
+                del gauges, ins, ts, outs
+                torch.cuda.empty_cache()
     if want("su3"):
         # mult_su3_mat_vec / mult_adj_su3_mat_vec over the 4V links of the lattice; like the
         # Dslash lines, `nstreams` independent batches in flight (graph branches), each

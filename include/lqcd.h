@@ -230,6 +230,31 @@ lq_status dslash_eo_multi(lq_context* ctx, int nlat, const lq_gauge* const* U, c
                           void* const* out, int out_parity, int nrhs, lq_prec vec_prec,
                           lq_stream stream);
 
+/* Paired colour-planar FP32 layout for several right-hand sides.  Right-hand sides are
+ * taken two at a time: pair p = 0 .. npair-1 (npair = (nrhs + 1) / 2) is three colour
+ * planes of Vh float4, element [p][c][site] = (Re v_2p, Re v_2p+1, Im v_2p, Im v_2p+1) of
+ * colour c at that site; npair * 3 * Vh * 16 bytes.  With odd nrhs the second half of the
+ * last pair is padding.  It is the layout of dslash_eo_paired.
+ *
+ * lq_vec_pair: canonical complex64 [nrhs][Vh][3] (in) -> paired (out); the padding half is
+ * written as zero.  lq_vec_unpair: paired (in) -> canonical (out); the padding half is not
+ * read.  Element copies, bit-exact.  Both device pointers 16-byte aligned, not overlapping;
+ * Vh >= 1, nrhs in [1, 16].  Asynchronous on `stream`. */
+lq_status lq_vec_pair(lq_context* ctx, int Vh, int nrhs, const void* in, void* out, lq_stream stream);
+lq_status lq_vec_unpair(lq_context* ctx, int Vh, int nrhs, const void* in, void* out, lq_stream stream);
+
+/* The half Dslash of dslash_eo (Eqs. (1.1)-(2.3) summed over the eight hops) for nrhs
+ * right-hand sides held in the paired layout (FP32 vectors and arithmetic; LQ_F32,
+ * LQ_BF16 or LQ_F16 links, 12 or 18 reals).  Each thread applies every loaded link element
+ * to two right-hand sides with one packed FP32x2 FMA, and loads each colour of a pair with
+ * one 16-byte access.  Same operator as dslash_eo with LQ_F32 vectors; the FMA order
+ * differs, so results agree within FP32 rounding, not bit for bit.
+ *   in, out: device, paired fields of U->Vh sites; must not overlap.  nrhs in [1, 16].
+ *   Errors: LQ_ERR_INVALID_ARG for an LQ_F64 gauge, NULL or misaligned pointers, a bad
+ *   parity or nrhs. */
+lq_status dslash_eo_paired(lq_context* ctx, const lq_gauge* U, const void* in, void* out,
+                           int out_parity, int nrhs, lq_stream stream);
+
 /* Improved staggered half Dslash with one-hop ("fat") links F and three-hop ("long",
  * Naik) links L -- the operator of the improved staggered application the paper times
  * (Table 4; the paper does not write it down):

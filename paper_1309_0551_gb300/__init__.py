@@ -90,6 +90,9 @@ def load(path: str | None = None):
                               ctypes.POINTER(lq_cg_stats), P], I),
         "dslash_force": ([P, P, D, P, P, P, P, ctypes.POINTER(D), P], I),
         "dslash_eo_multi": ([P, I, P, P, P, I, I, I, P], I),
+        "lq_vec_pair": ([P, I, I, P, P, P], I),
+        "lq_vec_unpair": ([P, I, I, P, P, P], I),
+        "dslash_eo_paired": ([P, P, P, P, I, I, P], I),
         "dslash_eo_improved": ([P, P, P, P, P, I, I, I, P], I),
         "lq_long_links": ([P, ctypes.POINTER(I), P, D, P, P], I),
         "su3_scalar_mult_add_batch": ([P, P, P, P, D, L, I, P], I),
@@ -266,6 +269,28 @@ def dslash_eo_multi(ctx: Context, Us, ins, outs, out_parity: int, nrhs: int = 1,
                                       (P * n)(*[t.data_ptr() for t in ins]),
                                       (P * n)(*[t.data_ptr() for t in outs]), int(out_parity), int(nrhs),
                                       int(vp), _stream(stream)))
+
+
+def paired_numel(Vh: int, nrhs: int) -> int:
+    """float32 elements of a paired colour-planar field: ((nrhs + 1) // 2) pairs x 3 colours
+    x Vh sites x 4 reals."""
+    return ((int(nrhs) + 1) // 2) * 3 * int(Vh) * 4
+
+
+def lq_vec_pair(ctx: Context, Vh: int, nrhs: int, inp, out, stream=None):
+    """Canonical complex64 [nrhs][Vh][3] -> paired colour-planar float32 layout."""
+    ctx.check(ctx.lib.lq_vec_pair(ctx.handle, int(Vh), int(nrhs), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def lq_vec_unpair(ctx: Context, Vh: int, nrhs: int, inp, out, stream=None):
+    """Paired colour-planar float32 layout -> canonical complex64 [nrhs][Vh][3]."""
+    ctx.check(ctx.lib.lq_vec_unpair(ctx.handle, int(Vh), int(nrhs), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def dslash_eo_paired(ctx: Context, U: Gauge, inp, out, out_parity: int, nrhs: int, stream=None):
+    """out = D inp on parity ``out_parity`` for ``nrhs`` right-hand sides in the paired layout."""
+    ctx.check(ctx.lib.dslash_eo_paired(ctx.handle, U.handle, _ptr(inp), _ptr(out), int(out_parity),
+                                       int(nrhs), _stream(stream)))
 
 
 def su3_mul_batch(ctx: Context, A, B, C, n=None, adjA=0, adjB=0, prec=None, stream=None):

@@ -28,6 +28,9 @@ constexpr int kTpsRhsWarps = 8;
 // TuneEntry::tps value that selects the link-staging kernel k_dslash_tma (one thread per
 // site, blocks of whole x-rows, links brought into shared memory by TMA bulk copies).
 constexpr int kTpsTma = 16;
+// TuneEntry::tps value of the paired-layout multi-RHS Dslash k_dslash_pr (rhs_tile = pairs
+// of right-hand sides per thread).
+constexpr int kTpsPaired = 32;
 
 // Flags of the context's device status word (lq_context::dev_status), set by kernels
 // whose bounded waits gave up; lq_sync reports and clears them.

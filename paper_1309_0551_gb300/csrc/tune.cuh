@@ -89,7 +89,7 @@ lq_status tune_pick(lq_context* ctx, const std::string& key, const std::vector<T
   // right-hand sides sharing each loaded link (per thread, or per block for the
   // rhs-per-warp kernel, which runs one thread per site and rhs), then the candidate order.
   const float tol = ctx->tune_mode == 2 ? 1.15f : 1.03f;
-  auto tps_of = [](const TuneEntry& t) { return t.tps == kTpsRhsWarps || t.tps == kTpsTma ? 1 : t.tps; };
+  auto tps_of = [](const TuneEntry& t) { return t.tps == kTpsRhsWarps || t.tps == kTpsTma || t.tps == kTpsPaired ? 1 : t.tps; };
   TuneEntry best;
   bool have = false;
   for (const TuneEntry& t : timed) {
