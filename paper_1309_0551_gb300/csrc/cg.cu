@@ -23,6 +23,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -82,13 +83,20 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, size_t str
   pdl_trigger();
 }
 
-// x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), grid-stride over
-// the rhs's 16-byte chunks.  The squares are summed in FP64.  (A TMA-tiled variant -- four bulk loads into shared memory, two
-// bulk stores -- measured slower than the grid-stride form: 21.8 vs 20.1 us FP32, 44 vs
-// 35 us FP64 at 32^4, with the per-site 8-byte accesses the grid-stride form then used.)
+// x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), about two
+// blocks per SM in all; each thread takes kUnroll chunks of its grid-stride sequence at a
+// time (all their loads in flight together).  FP64 vectors: every square is accumulated
+// in FP64.  FP32 vectors: each thread sums its squares in FP32 with Kahan compensation
+// (error at most ~2 u of the sum, u = 2^-24: the rounding of one FP32 value), a warp sums
+// its threads' values with the compensated FP32 tree (warp_sum), and the warps' sums are
+// reduced in FP64.  On GB300's FP64 pipe (1/64 of FP32) an FP64
+// conversion and add per real, or even per chunk, took as long as the memory traffic.
+// (A TMA-tiled variant -- four bulk loads into shared memory, two bulk stores -- measured
+// slower than the grid-stride form: 21.8 vs 20.1 us FP32, 44 vs 35 us FP64 at 32^4.)
+constexpr int kUnroll = 4;
 template <lq_prec VP>
-__global__ void __launch_bounds__(kBlas) k_cg_update(void* x, void* r, const void* p, const void* Ap,
-                                                     int Vh, Reducer red) {
+__global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const void* p, const void* Ap,
+                                                        int Vh, Reducer red) {
   using C = Chunk<VP>;
   using T = typename C::real;
   using V = typename C::vec;
@@ -97,33 +105,69 @@ __global__ void __launch_bounds__(kBlas) k_cg_update(void* x, void* r, const voi
   const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state) + rhs;
   const T alpha = (T)sc->alpha;
   double acc[1] = {0.0};
+  float ks = 0.f, kc = 0.f;   // FP32: compensated running sum (Kahan) and its correction
   const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
   V* xc = reinterpret_cast<V*>(x) + rhs * nch;
   V* rc = reinterpret_cast<V*>(r) + rhs * nch;
   const V* pc = reinterpret_cast<const V*>(p) + rhs * nch;
   const V* ac = reinterpret_cast<const V*>(Ap) + rhs * nch;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
-    T xv[C::n], rv[C::n], pv[C::n], av[C::n];
-    C::get(xc[i], xv);
-    C::get(rc[i], rv);
-    C::get(__ldg(pc + i), pv);
-    C::get(__ldg(ac + i), av);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
+    V xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
 #pragma unroll
-    for (int k = 0; k < C::n; ++k) {
-      xv[k] = fma(alpha, pv[k], xv[k]);
-      rv[k] = fma(-alpha, av[k], rv[k]);
-      acc[0] = fma((double)rv[k], (double)rv[k], acc[0]);
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i < nch) {
+        xw[u] = xc[i];
+        rw[u] = rc[i];
+        pw[u] = __ldg(pc + i);
+        aw[u] = __ldg(ac + i);
+      }
     }
-    xc[i] = C::put(xv);
-    rc[i] = C::put(rv);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i >= nch) continue;
+      T xv[C::n], rv[C::n], pv[C::n], av[C::n];
+      C::get(xw[u], xv);
+      C::get(rw[u], rv);
+      C::get(pw[u], pv);
+      C::get(aw[u], av);
+#pragma unroll
+      for (int k = 0; k < C::n; ++k) {
+        xv[k] = fma(alpha, pv[k], xv[k]);
+        rv[k] = fma(-alpha, av[k], rv[k]);
+      }
+      if constexpr (VP == LQ_F64) {
+#pragma unroll
+        for (int k = 0; k < C::n; ++k) acc[0] = fma((double)rv[k], (double)rv[k], acc[0]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < C::n; ++k) {
+          const float y = fmaf(rv[k], rv[k], -kc);
+          const float t = ks + y;
+          kc = (t - ks) - y;
+          ks = t;
+        }
+      }
+      xc[i] = C::put(xv);
+      rc[i] = C::put(rv);
+    }
   }
   pdl_trigger();
-  block_reduce<1>(acc, red, rhs, gridDim.y);
+  if constexpr (VP == LQ_F64) {
+    block_reduce<1>(acc, red, rhs, gridDim.y);
+  } else {
+    const float accf[1] = {ks - kc};   // the thread's sum, then the compensated warp tree
+    block_reduce<1>(accf, red, rhs, gridDim.y);
+  }
 }
 
-// p = r + beta p for active right-hand sides.  grid = (nbx, nrhs), 16-byte chunks.
+// p = r + beta p for active right-hand sides.  grid = (nbx, nrhs), about one wave of
+// blocks (four per SM) in all, 16-byte chunks, kUnroll chunks of the thread's grid-stride
+// sequence loaded together.
 template <lq_prec VP>
-__global__ void __launch_bounds__(kBlas) k_cg_xpay(const void* r, void* p, const CGScalars* sc, int Vh) {
+__global__ void __launch_bounds__(kBlas, 4) k_cg_xpay(const void* r, void* p, const CGScalars* sc, int Vh) {
   using C = Chunk<VP>;
   using T = typename C::real;
   using V = typename C::vec;
@@ -134,13 +178,29 @@ __global__ void __launch_bounds__(kBlas) k_cg_xpay(const void* r, void* p, const
     const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
     const V* rc = reinterpret_cast<const V*>(r) + rhs * nch;
     V* pc = reinterpret_cast<V*>(p) + rhs * nch;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
-      T rv[C::n], pv[C::n];
-      C::get(__ldg(rc + i), rv);
-      C::get(pc[i], pv);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    constexpr int kU = VP == LQ_F64 ? 2 : kUnroll;   // (FP64: four would spill)
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kU * stride) {
+      V rw[kU], pw[kU];
 #pragma unroll
-      for (int k = 0; k < C::n; ++k) pv[k] = fma(beta, pv[k], rv[k]);
-      pc[i] = C::put(pv);
+      for (int u = 0; u < kU; ++u) {
+        const size_t i = i0 + u * stride;
+        if (i < nch) {
+          rw[u] = __ldg(rc + i);
+          pw[u] = pc[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const size_t i = i0 + u * stride;
+        if (i >= nch) continue;
+        T rv[C::n], pv[C::n];
+        C::get(rw[u], rv);
+        C::get(pw[u], pv);
+#pragma unroll
+        for (int k = 0; k < C::n; ++k) pv[k] = fma(beta, pv[k], rv[k]);
+        pc[i] = C::put(pv);
+      }
     }
   }
   pdl_trigger();
@@ -545,7 +605,10 @@ lq_status launch_blas_update(Solver& S) {
     LQ_CHECK_LAUNCH(S.ctx, "k_seg_update");
     return LQ_OK;
   }
-  dim3 grid(S.nbx, S.nrhs);
+  // about two blocks per SM over all right-hand sides: fewer block reductions (FP64), each
+  // thread streaming more chunks
+  const int nb = std::min(S.nbx, std::max(1, (2 * S.ctx->num_sms + S.nrhs - 1) / S.nrhs));
+  dim3 grid(nb, S.nrhs);
   Reducer red = S.reducer(FIN_BETA);
   cudaError_t e = S.vp == LQ_F64
                       ? launch_k(k_cg_update<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
@@ -564,7 +627,8 @@ lq_status launch_xpay(Solver& S) {
     LQ_CHECK_LAUNCH(S.ctx, "k_seg_xpay");
     return LQ_OK;
   }
-  dim3 grid(S.nbx, S.nrhs);
+  const int nb = std::min(S.nbx, std::max(1, (4 * S.ctx->num_sms + S.nrhs - 1) / S.nrhs));
+  dim3 grid(nb, S.nrhs);
   cudaError_t e = S.vp == LQ_F64
                       ? launch_k(k_cg_xpay<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, (const void*)S.r, S.p,
                                  (const CGScalars*)S.sc, S.Vh)

@@ -29,11 +29,11 @@ __global__ void __launch_bounds__(256) k_dslash(const DslashKArgs a) {
   const int sub = gtid % TPS;
   const int rhs0 = ty * NR;
   const bool live = cb < a.G.Vh;
-  double part[NR];
+  T part[NR];   // the thread's share of a fused reduction (one site: FP32 in FP32 kernels)
   T acc[NR][6];
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    part[r] = 0.0;
+    part[r] = T(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[r][k] = T(0);
   }

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(256) k_dslash_multi(const MultiKArgs a) {
         skip &= system_skipped(c, a.skip_mode);
       }
     }
-    double part[NR];
+    T part[NR];   // FP32 kernels: summed per warp by the compensated FP32 tree
 #pragma unroll
-    for (int r = 0; r < NR; ++r) part[r] = 0.0;
+    for (int r = 0; r < NR; ++r) part[r] = T(0);
     if (!skip) {
       const int gtid = tx * blockDim.x + threadIdx.x;
       const int cb = gtid / TPS;
@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_multi_rw(const MultiKArgs a)
       }
     }
     const int cb = tx * 32 + lane;
-    double part[NRT];
+    float part[NRT];   // summed per warp by the compensated FP32 tree (warp_sum)
 #pragma unroll
-    for (int r = 0; r < NRT; ++r) part[r] = 0.0;
+    for (int r = 0; r < NRT; ++r) part[r] = 0.f;
     if (!skip) {
       const int cbc = cb < G.Vh ? cb : G.Vh - 1;
       int xh, row, x, y, z, t;

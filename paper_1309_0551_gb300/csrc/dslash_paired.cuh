@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(256, paired_min_blocks(NP)) k_dslash_pr(const 
     }
   }
   pdl_trigger();
-  double part[2 * NP];
+  float part[2 * NP];   // summed per warp by the compensated FP32 tree (warp_sum)
 #pragma unroll
-  for (int r = 0; r < 2 * NP; ++r) part[r] = 0.0;
+  for (int r = 0; r < 2 * NP; ++r) part[r] = 0.f;
   if (live) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256, paired_min_blocks(NP)) k_dslash_pr(const 
           }
         }
       }
-      part[2 * q] = (double)pa;
-      part[2 * q + 1] = (double)pb;
+      part[2 * q] = pa;
+      part[2 * q + 1] = pb;
     }
   }
   if constexpr (RED) {

@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(32 * RT) k_dslash_rw(const DslashKArgs a) {
       }
   }
   pdl_trigger();
-  double part[NRT];
+  float part[NRT];   // summed per warp by the compensated FP32 tree (warp_sum)
 #pragma unroll
-  for (int r = 0; r < NRT; ++r) part[r] = 0.0;
+  for (int r = 0; r < NRT; ++r) part[r] = 0.f;
   if (cb < G.Vh)
     dslash_epilogue<LQ_F32, NRT, 1>(acc, a.out, a.w1, a.a1, a.w2, a.a2, a.c, RED ? a.reduce : RED_NONE, a.rhs_stride,
                                     a.nrhs, rhs0, cb, 0, part);

@@ -156,11 +156,13 @@ __device__ __forceinline__ void dslash_combine(T (&acc)[NR][6]) {
 
 // out = c*acc + a1*w1 + a2*w2 for this lane's colour components; adds this lane's share of
 // Re<w1, out> (RED_DOT) or ||out||^2 (RED_NORM) to part[r].
-template <lq_prec VP, int NR, int TPS, class T>
+// part: the thread's running reduction per rhs, FP64 or (FP32 kernels) FP32, summed per
+// warp afterwards by warp_sum / block_reduce.
+template <lq_prec VP, int NR, int TPS, class T, class P>
 __device__ __forceinline__ void dslash_epilogue(const T (&acc)[NR][6], void* out, const void* w1, double a1,
                                                 const void* w2, double a2, double cc, int reduce,
                                                 size_t rhs_stride, int nrhs, int rhs0, int cb, int sub,
-                                                double (&part)[NR]) {
+                                                P (&part)[NR]) {
   using VT = VecT<VP>;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
@@ -189,7 +191,7 @@ __device__ __forceinline__ void dslash_epilogue(const T (&acc)[NR][6], void* out
         else if (reduce == RED_NORM)
           ps = fma(res[0], res[0], fma(res[1], res[1], ps));
       }
-      part[r] += (double)ps;
+      part[r] += (P)ps;
     }
   }
 }

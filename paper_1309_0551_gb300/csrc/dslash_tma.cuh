@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_dslash_tma(const DslashKArgs a, int T) 
       else mat_vec_acc(u, v[h], acc, sg[h]);
     }
     float res[6];
-    double part[1] = {0.0};
+    float part[1] = {0.f};
 #pragma unroll
     for (int k = 0; k < 6; ++k) res[k] = (float)a.c * acc[k];
     float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -191,11 +191,12 @@ __global__ void __launch_bounds__(256) k_dslash_tma(const DslashKArgs a, int T) 
     }
     if (ok) VT::store(a.out, voff + cb, res);   // a block whose links did not arrive writes nothing
     if constexpr (RED) {
-      // the site's share in the working precision (six products), summed over sites in FP64
+      // the site's share in the working precision (six products), summed per warp by the
+      // compensated FP32 tree and in FP64 from there
       float ps = 0.f;
 #pragma unroll
       for (int k = 0; k < 6; ++k) ps = fmaf(a.reduce == RED_DOT ? w[k] : res[k], res[k], ps);
-      part[0] = ok ? (double)ps : 0.0;
+      part[0] = ok ? ps : 0.f;
       block_sum_store<1>(part, a.red.partials + (size_t)rhs * gridDim.x + blockIdx.x, 1, 1);
     }
   }

@@ -157,6 +157,29 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Sum over the warp of FP32 values, returned in FP64 (valid in every lane).  A fixed xor
+// shuffle tree of error-free FP32 pair sums -- Knuth's TwoSum: t = a + b rounded and
+// e = (a - (t - b')) + (b - b'), b' = t - a, with t + e = a + b exactly -- keeps each
+// level's rounding error in a companion term c; s + c is formed in FP64 once.  The result
+// is the exact sum of the 32 values up to ~32 u^2 relative (u = 2^-24), i.e. as good as
+// an FP64 tree over them, with two conversions and one FP64 add per warp instead of five
+// shuffled FP64 adds: GB300's FP64 pipe runs at 1/64 of the FP32 rate, and in the CG's
+// fused Dslash reduction the FP64 tree kept it a quarter busy.
+__device__ __forceinline__ double warp_sum(float x) {
+  float s = x, c = 0.f;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    s = t;
+    c = (c + c2) + e;
+  }
+  return (double)s + (double)c;
+}
+
 // The block-wide helpers below (block_reduce, block_total, block_sum_store, grid_finish)
 // take threadIdx.x as the thread's index in the block: they need one-dimensional blocks.
 //
@@ -168,8 +191,10 @@ __device__ __forceinline__ double warp_sum(double x) {
 // kWideFinish: the last block sums each row with all its threads (short tail; for kernels
 // that finish every launch, like the CG update) or one warp per row (fewer registers for
 // the whole kernel: the compiler sizes it for this rarely run path too).
-template <int NR, bool kWideFinish = true>
-__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs,
+// v: per-thread contributions in FP64, or in FP32 (then summed per warp by the compensated
+// FP32 tree, FP64 from the warp sums up).
+template <int NR, bool kWideFinish = true, class VT>
+__device__ __forceinline__ void block_reduce(const VT (&v)[NR], const Reducer& red, int rhs0, int nrhs,
                                              int bx, int nbx) {
   __shared__ double sm[NR][32];
   __shared__ int am_last;
@@ -249,15 +274,15 @@ __device__ __forceinline__ double block_total(const double* row, int n) {
 }
 
 // The one-dimensional form: column = blockIdx.x of a (nbx, rhs tiles) grid.
-template <int NR>
-__device__ __forceinline__ void block_reduce(const double (&v)[NR], const Reducer& red, int rhs0, int nrhs) {
-  block_reduce<NR>(v, red, rhs0, nrhs, blockIdx.x, gridDim.x);
+template <int NR, class VT>
+__device__ __forceinline__ void block_reduce(const VT (&v)[NR], const Reducer& red, int rhs0, int nrhs) {
+  block_reduce<NR, true>(v, red, rhs0, nrhs, blockIdx.x, gridDim.x);
 }
 
 // Block-wide sums of v[r] (every thread calls); thread 0 stores sum r at dst[r * stride]
 // for r < nvalid.  Ends with a barrier so shared memory can be reused by the next call.
-template <int NR>
-__device__ __forceinline__ void block_sum_store(const double (&v)[NR], double* dst, size_t stride, int nvalid) {
+template <int NR, class VT>
+__device__ __forceinline__ void block_sum_store(const VT (&v)[NR], double* dst, size_t stride, int nvalid) {
   __shared__ double sm[NR][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -279,8 +304,8 @@ __device__ __forceinline__ void block_sum_store(const double (&v)[NR], double* d
 
 // Block-wide sums of v[r] added to dst[r] for r < nvalid by one thread (every thread
 // calls; deterministic: a fixed tree per block, one writer).  Ends with a barrier.
-template <int NR>
-__device__ __forceinline__ void block_sum_add(const double (&v)[NR], double* dst, int nvalid) {
+template <int NR, class VT>
+__device__ __forceinline__ void block_sum_add(const VT (&v)[NR], double* dst, int nvalid) {
   __shared__ double sm[NR][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
