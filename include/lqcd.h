@@ -437,8 +437,8 @@ lq_status cg_solve_batched(lq_context* ctx, int nlat, const lq_gauge* const* U_h
  *   at each check.  Launch shapes come from the context's tuning table when an earlier
  *   call (e.g. cg_solve with the same gauges) filled it, else fixed defaults.
  *   Limit: (4 inner vectors, 5 with U_lo) * nrhs * Vh * 48 bytes (24 with U_lo) + 2 FP64
- *   vectors of nrhs * Vh * 48 bytes + 3 * nrhs * Vh/16 * 8 bytes of partials must fit in
- *   32 MiB (e.g. a 16^4 lattice with one right-hand side); larger problems get
+ *   vectors of nrhs * Vh * 48 bytes + 3 * nrhs * Vh/16 * 8 + nrhs * 256 bytes of partials
+ *   must fit in 32 MiB (e.g. a 16^4 lattice with one right-hand side); larger problems get
  *   LQ_ERR_INVALID_ARG with a message naming the sizes.
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *   and caches it; make that first call before any stream capture.

@@ -5,8 +5,10 @@
 //   xpay    p = r + beta p                      (skipped for inactive right-hand sides)
 //   dslash  t = D_oe p                          (odd sites)
 //   dslash  Ap = m^2 p - D_eo t, <p, Ap>        (fused epilogue; per-block partials only)
-//   alpha   alpha = rr / <p,Ap>                 (one block per rhs sums the partials)
-//   update  x += alpha p, r -= alpha Ap, rr = ||r||^2 (last block forms beta, stop flag)
+//   pap     <p,Ap> group sums                   (32 blocks per rhs over the partials)
+//   update  alpha = rr / <p,Ap> in every block, x += alpha p, r -= alpha Ap,
+//           rr = ||r||^2 (last block forms beta, stop flag)
+// (The batched solve forms alpha with k_cg_alpha, one block per system, instead.)
 // All scalars stay on the device.  `check_every` iterations are captured once as a CUDA
 // graph and replayed; between replays the host reads the per-rhs scalars (one small
 // device-to-host copy) and decides on reliable updates and termination.
@@ -83,6 +85,22 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, size_t str
   pdl_trigger();
 }
 
+// <p,Ap> of the single-lattice solve in two stages, without a one-block launch: block g
+// of a system sums columns g, g + kPapGroups, ... of the D_eo partials (FIN_DEFER) into
+// gsum[rhs][g]; every block of k_cg_update then sums the kPapGroups values itself, in the
+// same order (the same alpha in every block).  (k_cg_alpha, one 1024-thread block per
+// system, spent ~7 us per iteration at 32^4 in its FP64 tree on one SM.)
+constexpr int kPapGroups = 32;
+__global__ void __launch_bounds__(256) k_cg_pap(const double* pap, size_t stride, int cols, double* gsum) {
+  pdl_wait();
+  const int rhs = blockIdx.y, g = blockIdx.x;
+  const double* row = pap + (size_t)rhs * stride;
+  double v[1] = {0.0};
+  for (int b = g + kPapGroups * (int)threadIdx.x; b < cols; b += kPapGroups * (int)blockDim.x) v[0] += __ldcg(row + b);
+  pdl_trigger();
+  block_sum_store<1>(v, gsum + (size_t)rhs * kPapGroups + g, 1, 1);
+}
+
 // x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA.  grid = (nbx, nrhs), about two
 // blocks per SM in all; each thread takes kUnroll chunks of its grid-stride sequence at a
 // time (all their loads in flight together).  FP64 vectors: every square is accumulated
@@ -96,14 +114,31 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* pap, size_t str
 constexpr int kUnroll = 4;
 template <lq_prec VP>
 __global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const void* p, const void* Ap,
-                                                        int Vh, Reducer red) {
+                                                        const double* gsum, int Vh, Reducer red) {
   using C = Chunk<VP>;
   using T = typename C::real;
   using V = typename C::vec;
   const int rhs = blockIdx.y;
   pdl_wait();
-  const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state) + rhs;
-  const T alpha = (T)sc->alpha;
+  CGScalars* sc = reinterpret_cast<CGScalars*>(red.finisher_state) + rhs;
+  // alpha = rr / <p,Ap> from the kPapGroups group sums (block 0 records it in the state;
+  // the FIN_BETA finisher at the end reads none of these fields)
+  __shared__ double s_alpha;
+  if (threadIdx.x < 32) {
+    double v = kPapGroups == 32 ? __ldcg(gsum + (size_t)rhs * kPapGroups + threadIdx.x) : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      const double a = (sc->active && v > 0.0) ? sc->rr / v : 0.0;
+      s_alpha = a;
+      if (blockIdx.x == 0) {
+        sc->pAp = v;
+        sc->alpha = a;
+        if (sc->active) sc->alpha_last = a;
+      }
+    }
+  }
+  __syncthreads();
+  const T alpha = (T)s_alpha;
   double acc[1] = {0.0};
   float ks = 0.f, kc = 0.f;   // FP32: compensated running sum (Kahan) and its correction
   const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
@@ -499,7 +534,8 @@ struct Solver {
   CGScalars* sc_host;    // pinned
   double* result;        // device [nrhs]
   double* partials;
-  double* dpartials;     // [nrhs][nblocks_max]: <p,Ap> partials of D_eo, summed by k_cg_alpha
+  double* dpartials;     // [nrhs][nblocks_max]: <p,Ap> partials of D_eo (k_cg_pap / k_cg_alpha)
+  double* gsum;          // [nrhs][kPapGroups]: <p,Ap> group sums (k_cg_pap -> k_cg_update)
   unsigned int* counter;
   int nblocks_max;
   bool pdl = false;      // programmatic dependent launch for the iteration kernels
@@ -612,9 +648,9 @@ lq_status launch_blas_update(Solver& S) {
   Reducer red = S.reducer(FIN_BETA);
   cudaError_t e = S.vp == LQ_F64
                       ? launch_k(k_cg_update<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
-                                 (const void*)S.Ap, S.Vh, red)
+                                 (const void*)S.Ap, (const double*)S.gsum, S.Vh, red)
                       : launch_k(k_cg_update<LQ_F32>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
-                                 (const void*)S.Ap, S.Vh, red);
+                                 (const void*)S.Ap, (const double*)S.gsum, S.Vh, red);
   if (e != cudaSuccess) return lq_cuda_fail(S.ctx, e, "k_cg_update");
   return LQ_OK;
 }
@@ -671,9 +707,9 @@ lq_status iteration(Solver& S) {
   e.red = &red;
   st = launch_dslash(S.ctx, e, S.s);
   if (st) return st;
-  cudaError_t ce = launch_k(k_cg_alpha, dim3(S.nrhs), dim3(1024), 0, S.s, S.pdl, (const double*)S.dpartials,
-                            (size_t)red.cols, red.cols, S.sc);
-  if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cg_alpha");
+  cudaError_t ce = launch_k(k_cg_pap, dim3(kPapGroups, S.nrhs), dim3(256), 0, S.s, S.pdl, (const double*)S.dpartials,
+                            (size_t)red.cols, red.cols, S.gsum);
+  if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cg_pap");
   return launch_blas_update(S);
 }
 
@@ -1049,7 +1085,8 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
 
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = 5 * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 16) + 8 +
-                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
+                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + (size_t)nrhs * kPapGroups * sizeof(double) +
+                      14 * 256;
   void* base = nullptr;
   lq_status st = lq_scratch(ctx, need, &base);
   if (st) return st;
@@ -1066,6 +1103,7 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * 2 * nrhs * S.nblocks_max);
   S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.gsum = (double*)A.take(sizeof(double) * nrhs * kPapGroups);
   if (A.off > need) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   st = host_scalars(ctx, nrhs);
   if (st) return st;
@@ -1170,7 +1208,8 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
   const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
   const size_t need = (S.mixed ? 5 : 4) * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 16) + 8 +
-                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + 13 * 256;
+                      3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + (size_t)nrhs * kPapGroups * sizeof(double) +
+                      14 * 256;
   if (need > kNoAllocScratchBytes)
     return lq_fail(ctx, LQ_ERR_INVALID_ARG,
                    "cg_solve_noalloc: %d right-hand sides on %d sites per parity need %zu bytes of scratch, "
@@ -1191,6 +1230,7 @@ extern "C" lq_status cg_solve_noalloc(lq_context* ctx, const lq_gauge* U_hi, con
   S.counter = (unsigned int*)A.take(sizeof(unsigned int));
   S.partials = (double*)A.take(sizeof(double) * 2 * nrhs * S.nblocks_max);
   S.dpartials = (double*)A.take(sizeof(double) * nrhs * S.nblocks_max);
+  S.gsum = (double*)A.take(sizeof(double) * nrhs * kPapGroups);
   if (A.off > kNoAllocScratchBytes) return lq_fail(ctx, LQ_ERR_INVALID_ARG, "internal: scratch layout overflow");
   CGScalars host_scalars[16];  // pageable host copy of the per-rhs scalars
   S.sc_host = host_scalars;
