@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <vector>
 
 #include "dslash_multi.cuh"
@@ -360,11 +361,14 @@ __global__ void __launch_bounds__(kBlas) k_seg_update(void* x, void* r, const vo
   using VT = VecT<VP>;
   using T = typename VT::real;
   const CGScalars* sc = reinterpret_cast<const CGScalars*>(red.finisher_state);
+  using A = typename std::conditional<VP == LQ_F64, double, float>::type;
   for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     int q, chunk, Vh, l;
     size_t base;
     seg_locate(g, tile, q, base, chunk, Vh, l);
-    double acc[1] = {0.0};
+    // FP32 vectors: the site's squares in FP32, the tile's sum by the compensated FP32
+    // block tree (block_sum_f32) and FP64 above
+    A acc[1] = {A(0)};
     const int i = chunk * kBlas + threadIdx.x;
     if (sc[q].active && i < Vh) {
       const T alpha = (T)sc[q].alpha;
@@ -380,7 +384,14 @@ __global__ void __launch_bounds__(kBlas) k_seg_update(void* x, void* r, const vo
       }
       VT::store(x, base + i, xv);
       VT::store(r, base + i, rv);
-      acc[0] = site_norm2(rv);
+      if constexpr (VP == LQ_F64) {
+        acc[0] = site_norm2(rv);
+      } else {
+        float s2 = rv[0] * rv[0];
+#pragma unroll
+        for (int k = 1; k < 6; ++k) s2 = fmaf(rv[k], rv[k], s2);
+        acc[0] = s2;
+      }
     }
     block_sum_store<1>(acc, red.partials + (size_t)q * g.pstride + chunk, g.pstride, 1);
   }

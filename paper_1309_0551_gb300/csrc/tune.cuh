@@ -3,6 +3,7 @@
 #pragma once
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lqcd_internal.cuh"
@@ -165,8 +166,7 @@ __device__ __forceinline__ double warp_sum(double x) {
 // an FP64 tree over them, with two conversions and one FP64 add per warp instead of five
 // shuffled FP64 adds: GB300's FP64 pipe runs at 1/64 of the FP32 rate, and in the CG's
 // fused Dslash reduction the FP64 tree kept it a quarter busy.
-__device__ __forceinline__ double warp_sum(float x) {
-  float s = x, c = 0.f;
+__device__ __forceinline__ void warp_sum_sc(float& s, float& c) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
@@ -177,7 +177,33 @@ __device__ __forceinline__ double warp_sum(float x) {
     s = t;
     c = (c + c2) + e;
   }
+}
+__device__ __forceinline__ double warp_sum(float x) {
+  float s = x, c = 0.f;
+  warp_sum_sc(s, c);
   return (double)s + (double)c;
+}
+
+// Block-wide sum of one FP32 value per thread, in FP64 (every thread gets it): the
+// compensated warp tree in each warp, the warps' (s, c) pairs through shared memory, the
+// same tree over them in warp 0 -- three FP64 operations per block.  Ends with a barrier.
+__device__ __forceinline__ double block_sum_f32(float x) {
+  __shared__ float2 sm[32];
+  __shared__ double total;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float s = x, c = 0.f;
+  warp_sum_sc(s, c);
+  if (lane == 0) sm[warp] = make_float2(s, c);
+  __syncthreads();
+  if (warp == 0) {
+    const float2 v = lane < nw ? sm[lane] : make_float2(0.f, 0.f);
+    s = v.x;
+    c = v.y;
+    warp_sum_sc(s, c);
+    if (lane == 0) total = (double)s + (double)c;
+  }
+  __syncthreads();
+  return total;
 }
 
 // The block-wide helpers below (block_reduce, block_total, block_sum_store, grid_finish)
@@ -283,6 +309,14 @@ __device__ __forceinline__ void block_reduce(const VT (&v)[NR], const Reducer& r
 // for r < nvalid.  Ends with a barrier so shared memory can be reused by the next call.
 template <int NR, class VT>
 __device__ __forceinline__ void block_sum_store(const VT (&v)[NR], double* dst, size_t stride, int nvalid) {
+  if constexpr (std::is_same<VT, float>::value) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const double t = block_sum_f32(v[r]);
+      if (threadIdx.x == 0 && r < nvalid) dst[(size_t)r * stride] = t;
+    }
+    return;
+  }
   __shared__ double sm[NR][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -306,6 +340,14 @@ __device__ __forceinline__ void block_sum_store(const VT (&v)[NR], double* dst, 
 // calls; deterministic: a fixed tree per block, one writer).  Ends with a barrier.
 template <int NR, class VT>
 __device__ __forceinline__ void block_sum_add(const VT (&v)[NR], double* dst, int nvalid) {
+  if constexpr (std::is_same<VT, float>::value) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const double t = block_sum_f32(v[r]);
+      if (threadIdx.x == 0 && r < nvalid) dst[r] += t;
+    }
+    return;
+  }
   __shared__ double sm[NR][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
