@@ -361,6 +361,10 @@ typedef struct {
  *         its iterated residual meets tol but its true residual does not.
  *   b, x: device complex128 [nrhs][Vh][3]; x is overwritten.  nrhs in [1, 16].
  *   stats: host array of nrhs entries (may be NULL).
+ *   With U_lo and nrhs >= 2 the inner vectors are kept in the paired colour-planar layout
+ *   of dslash_eo_paired (converted to and from the canonical layout only at the reliable
+ *   updates); the environment variable LQCD_CG_PAIRED=0 keeps them canonical.  Both reach
+ *   the same tolerance; iterates differ by FP32 rounding order.
  * Synchronises `stream` at each check (every check_every iterations).  Returns
  * LQ_ERR_NOT_CONVERGED if maxiter was reached (stats filled in), LQ_ERR_NUMERIC if b or a
  * residual holds NaN/Inf, LQ_ERR_TIMEOUT if the context's device status word holds a

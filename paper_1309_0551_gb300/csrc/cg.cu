@@ -23,6 +23,7 @@
 // the rounded operator into it: with BF16 links on Haar links at m = 0.01 that form
 // stalls near 1e-4, this one reaches 1e-10 (flexible CG: Golub & Ye 1999, Notay 2000).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -31,12 +32,16 @@
 #include <vector>
 
 #include "dslash_multi.cuh"
+#include "dslash_paired.cuh"
 #include "lqcd_internal.cuh"
 #include "tune.cuh"
 
 bool dslash_vec_ok(lq_prec gauge, lq_prec vec);
 lq_status launch_dslash_multi(lq_context* ctx, MultiKArgs a, lq_prec gp, int recon, lq_prec vp,
                               const std::string& key, cudaStream_t s);
+lq_status launch_dslash_paired(lq_context* ctx, const lq_gauge* U, PairedKArgs k, int red_cols_max, int* cols_out,
+                               cudaStream_t s);
+PairedKArgs make_paired_kargs(const lq_gauge* U, const void* in, void* out, int out_parity, int nrhs);
 
 namespace {
 
@@ -322,6 +327,128 @@ __global__ void __launch_bounds__(kBlas) k_fold(double* x_hi, void* x_lo, int Vh
 }
 
 
+// ------------------------------------------------- paired-layout (multi-RHS) kernels ---
+//
+// The multi-RHS mixed solve keeps its FP32 inner vectors in the paired colour-planar
+// layout of dslash_eo_paired: pair pr = (rhs 2 pr, 2 pr + 1) is 3 Vh float4 chunks
+// (Re a, Re b, Im a, Im b); lanes x, z belong to rhs a, y, w to rhs b.  A padding half (odd
+// nrhs) is never active: its scalars are not read, its partials not stored.
+
+// p = r + beta p for the active right-hand sides of each pair.  grid = (nbx, npair).
+__global__ void __launch_bounds__(kBlas, 4) k_cgp_xpay(const float4* r, float4* p, const CGScalars* sc, int Vh,
+                                                       int nrhs) {
+  const int pr = blockIdx.y, ra = 2 * pr, rb = 2 * pr + 1;
+  pdl_wait();
+  const bool actA = sc[ra].active != 0, actB = rb < nrhs && sc[rb].active != 0;
+  if (actA || actB) {
+    const float bA = actA ? (float)sc[ra].beta : 0.f, bB = actB ? (float)sc[rb].beta : 0.f;
+    const size_t nch = (size_t)3 * Vh;
+    const float4* rc = r + pr * nch;
+    float4* pc = p + pr * nch;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
+      float4 rw[kUnroll], pw[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const size_t i = i0 + u * stride;
+        if (i < nch) {
+          rw[u] = __ldg(rc + i);
+          pw[u] = pc[i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const size_t i = i0 + u * stride;
+        if (i >= nch) continue;
+        float4 q = pw[u];
+        if (actA) {
+          q.x = fmaf(bA, q.x, rw[u].x);
+          q.z = fmaf(bA, q.z, rw[u].z);
+        }
+        if (actB) {
+          q.y = fmaf(bB, q.y, rw[u].y);
+          q.w = fmaf(bB, q.w, rw[u].w);
+        }
+        pc[i] = q;
+      }
+    }
+  }
+  pdl_trigger();
+}
+
+// x += alpha p; r -= alpha Ap; ||r||^2 -> FIN_BETA, per rhs of each pair, alpha of each
+// rhs from its kPapGroups group sums of <p,Ap> (as k_cg_update).  grid = (nbx, npair).
+__global__ void __launch_bounds__(kBlas, 2) k_cgp_update(float4* x, float4* r, const float4* p, const float4* Ap,
+                                                         const double* gsum, int Vh, int nrhs, Reducer red) {
+  const int pr = blockIdx.y;
+  pdl_wait();
+  CGScalars* sc = reinterpret_cast<CGScalars*>(red.finisher_state);
+  __shared__ double s_alpha[2];
+  if (threadIdx.x < 64) {   // warp 0: rhs 2 pr, warp 1: rhs 2 pr + 1
+    const int h = threadIdx.x >> 5, rh = 2 * pr + h;
+    double v = rh < nrhs ? __ldcg(gsum + (size_t)rh * kPapGroups + (threadIdx.x & 31)) : 0.0;
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) {
+      double a = 0.0;
+      if (rh < nrhs) {
+        CGScalars* c = sc + rh;
+        a = (c->active && v > 0.0) ? c->rr / v : 0.0;
+        if (blockIdx.x == 0) {
+          c->pAp = v;
+          c->alpha = a;
+          if (c->active) c->alpha_last = a;
+        }
+      }
+      s_alpha[h] = a;
+    }
+  }
+  __syncthreads();
+  const float aA = (float)s_alpha[0], aB = (float)s_alpha[1];
+  float sA = 0.f, cA = 0.f, sB = 0.f, cB = 0.f;   // Kahan sums of each rhs's squares
+  auto kahan = [](float& s_, float& c_, float v) {
+    const float y = v - c_;
+    const float t = s_ + y;
+    c_ = (t - s_) - y;
+    s_ = t;
+  };
+  const size_t nch = (size_t)3 * Vh;
+  float4* xc = x + pr * nch;
+  float4* rc = r + pr * nch;
+  const float4* pc = p + pr * nch;
+  const float4* ac = Ap + pr * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
+    float4 xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i < nch) {
+        xw[u] = xc[i];
+        rw[u] = rc[i];
+        pw[u] = __ldg(pc + i);
+        aw[u] = __ldg(ac + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = i0 + u * stride;
+      if (i >= nch) continue;
+      float4 xv = xw[u], rv = rw[u];
+      xv.x = fmaf(aA, pw[u].x, xv.x); xv.z = fmaf(aA, pw[u].z, xv.z);
+      xv.y = fmaf(aB, pw[u].y, xv.y); xv.w = fmaf(aB, pw[u].w, xv.w);
+      rv.x = fmaf(-aA, aw[u].x, rv.x); rv.z = fmaf(-aA, aw[u].z, rv.z);
+      rv.y = fmaf(-aB, aw[u].y, rv.y); rv.w = fmaf(-aB, aw[u].w, rv.w);
+      kahan(sA, cA, fmaf(rv.x, rv.x, rv.z * rv.z));
+      kahan(sB, cB, fmaf(rv.y, rv.y, rv.w * rv.w));
+      xc[i] = xv;
+      rc[i] = rv;
+    }
+  }
+  pdl_trigger();
+  const float acc[2] = {sA - cA, sB - cB};
+  block_reduce<2>(acc, red, 2 * pr, nrhs, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------- segmented (multi-lattice) kernels -
 //
 // The batched solver keeps every vector of all its lattices in one concatenated array:
@@ -533,6 +660,7 @@ struct Solver {
   const lq_gauge* Ulo;   // == Uhi for the plain FP64 solve
   lq_prec vp;            // inner vector precision
   bool mixed;
+  bool paired = false;   // FP32 inner vectors in the paired colour-planar layout (nrhs >= 2)
   double mass;
   int nrhs, Vh, nbx;
   const double* b;
@@ -558,6 +686,8 @@ struct Solver {
     return Reducer{partials, counter, result, nblocks_max, fin, (void*)sc};
   }
   size_t vbytes(lq_prec q) const { return sites * 6 * lq_prec_bytes(q); }
+  // bytes of one inner vector: canonical, or paired (an odd nrhs pads its last pair)
+  size_t vin_bytes() const { return paired ? (size_t)((nrhs + 1) / 2) * 3 * Vh * 16 : vbytes(vp); }
 };
 
 // ---- batched (multi-lattice) versions of the solver steps
@@ -686,7 +816,44 @@ lq_status launch_xpay(Solver& S) {
 }
 
 // One inner iteration.
+// One inner iteration on the paired layout: xpay, D_oe and D_eo with <p,Ap> in the paired
+// kernel, the group sums, the update.
+lq_status iteration_paired(Solver& S) {
+  const int npair = (S.nrhs + 1) / 2;
+  {
+    const int nb = std::min(S.nbx, std::max(1, (4 * S.ctx->num_sms + npair - 1) / npair));
+    cudaError_t e = launch_k(k_cgp_xpay, dim3(nb, npair), dim3(kBlas), 0, S.s, S.pdl, (const float4*)S.r,
+                             (float4*)S.p, (const CGScalars*)S.sc, S.Vh, S.nrhs);
+    if (e != cudaSuccess) return lq_cuda_fail(S.ctx, e, "k_cgp_xpay");
+  }
+  PairedKArgs d = make_paired_kargs(S.Ulo, S.p, S.t, 1, S.nrhs);
+  d.pdl = S.pdl ? 1 : 0;
+  lq_status st = launch_dslash_paired(S.ctx, S.Ulo, d, 0, nullptr, S.s);
+  if (st) return st;
+  PairedKArgs e = make_paired_kargs(S.Ulo, S.t, S.Ap, 0, S.nrhs);
+  e.pdl = S.pdl ? 1 : 0;
+  e.w1 = (const float4*)S.p;
+  e.a1 = (float)(S.mass * S.mass);
+  e.c = -1.f;
+  e.reduce = RED_DOT;
+  e.red = S.reducer(FIN_DEFER);
+  e.red.partials = S.dpartials;
+  int cols = 0;
+  st = launch_dslash_paired(S.ctx, S.Ulo, e, S.nblocks_max, &cols, S.s);
+  if (st) return st;
+  cudaError_t ce = launch_k(k_cg_pap, dim3(kPapGroups, S.nrhs), dim3(256), 0, S.s, S.pdl, (const double*)S.dpartials,
+                            (size_t)cols, cols, S.gsum);
+  if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cg_pap");
+  const int nb = std::min(S.nbx, std::max(1, (2 * S.ctx->num_sms + npair - 1) / npair));
+  ce = launch_k(k_cgp_update, dim3(nb, npair), dim3(kBlas), 0, S.s, S.pdl, (float4*)S.xl, (float4*)S.r,
+                (const float4*)S.p, (const float4*)S.Ap, (const double*)S.gsum, S.Vh, S.nrhs,
+                S.reducer(FIN_BETA));
+  if (ce != cudaSuccess) return lq_cuda_fail(S.ctx, ce, "k_cgp_update");
+  return LQ_OK;
+}
+
 lq_status iteration(Solver& S) {
+  if (S.paired) return iteration_paired(S);
   lq_status st = launch_xpay(S);
   if (st) return st;
   if (S.batch) {
@@ -762,6 +929,15 @@ lq_status fold_x(Solver& S) {
     return LQ_OK;
   }
   dim3 grid(S.nbx, S.nrhs);
+  if (S.paired) {
+    // x_lo to the canonical layout in t, folded from there; x_lo = 0
+    lq_status st = lq_vec_unpair(S.ctx, S.Vh, S.nrhs, S.xl, S.t, S.s);
+    if (st) return st;
+    k_fold<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.x, S.t, S.Vh);
+    LQ_CHECK_LAUNCH(S.ctx, "k_fold");
+    LQ_CUDA(S.ctx, cudaMemsetAsync(S.xl, 0, S.vin_bytes(), S.s));
+    return LQ_OK;
+  }
   k_fold<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.x, S.xl, S.Vh);
   LQ_CHECK_LAUNCH(S.ctx, "k_fold");
   return LQ_OK;
@@ -781,6 +957,24 @@ lq_status replace_residual(Solver& S, bool with_dot) {
   }
   dim3 grid(S.nbx, S.nrhs);
   const CGScalars* sc = S.sc;
+  if (S.paired) {
+    // In the canonical layout, in x_lo (zero after the fold that precedes every
+    // replacement, free until the next iteration) and t: r_old and Ap in, r_new out, then
+    // back to the paired r; x_lo = 0 again.
+    lq_status st;
+    if (with_dot) {
+      st = lq_vec_unpair(S.ctx, S.Vh, S.nrhs, S.r, S.xl, S.s);
+      if (st) return st;
+      st = lq_vec_unpair(S.ctx, S.Vh, S.nrhs, S.Ap, S.t, S.s);
+      if (st) return st;
+    }
+    k_cg_replace<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.rhi, S.xl, S.t, sc, S.Vh, with_dot ? 1 : 0, red);
+    LQ_CHECK_LAUNCH(S.ctx, "k_cg_replace");
+    st = lq_vec_pair(S.ctx, S.Vh, S.nrhs, S.xl, S.r, S.s);
+    if (st) return st;
+    LQ_CUDA(S.ctx, cudaMemsetAsync(S.xl, 0, S.vin_bytes(), S.s));
+    return LQ_OK;
+  }
   if (S.mixed) k_cg_replace<LQ_F32><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, sc, S.Vh, with_dot ? 1 : 0, red);
   else k_cg_replace<LQ_F64><<<grid, kBlas, 0, S.s>>>(S.rhi, S.r, S.Ap, sc, S.Vh, with_dot ? 1 : 0, red);
   LQ_CHECK_LAUNCH(S.ctx, "k_cg_replace");
@@ -878,8 +1072,8 @@ lq_status run_solver(Solver& S, const lq_cg_params& P, lq_cg_stats* stats, int* 
 
   // ---- initial state: x = 0, r = p = 0, r_hi = b, r = round(b), rr = ||r||^2
   LQ_CUDA(ctx, cudaMemsetAsync(S.x, 0, S.vbytes(LQ_F64), S.s));
-  if (S.mixed) LQ_CUDA(ctx, cudaMemsetAsync(S.xl, 0, S.vbytes(S.vp), S.s));
-  LQ_CUDA(ctx, cudaMemsetAsync(S.p, 0, S.vbytes(S.vp), S.s));
+  if (S.mixed) LQ_CUDA(ctx, cudaMemsetAsync(S.xl, 0, S.vin_bytes(), S.s));
+  LQ_CUDA(ctx, cudaMemsetAsync(S.p, 0, S.vin_bytes(), S.s));
   st = copy_source(S);
   if (st) return st;
   st = read_result(S, res);
@@ -1093,8 +1287,14 @@ extern "C" lq_status cg_solve(lq_context* ctx, const lq_gauge* U_hi, const lq_ga
   if (S.nbx > 8 * ctx->num_sms) S.nbx = 8 * ctx->num_sms;
   S.nblocks_max = (S.Vh + 15) / 16;  // Dslash reductions: up to 4 threads per site, blocks of 64
   if (S.nblocks_max < S.nbx) S.nblocks_max = S.nbx;
+  // Two or more right-hand sides with reduced-precision links iterate on the paired
+  // colour-planar layout (the environment variable LQCD_CG_PAIRED=0 keeps the canonical one)
+  {
+    const char* e = getenv("LQCD_CG_PAIRED");
+    S.paired = S.mixed && nrhs >= 2 && S.Ulo->prec != LQ_F64 && !(e && e[0] == '0');
+  }
 
-  const size_t vin = S.vbytes(S.vp), v64 = S.vbytes(LQ_F64);
+  const size_t vin = S.vin_bytes(), v64 = S.vbytes(LQ_F64);
   const size_t need = 5 * vin + 2 * v64 + nrhs * (sizeof(CGScalars) + 16) + 8 +
                       3 * (size_t)nrhs * S.nblocks_max * sizeof(double) + (size_t)nrhs * kPapGroups * sizeof(double) +
                       14 * 256;
