@@ -707,6 +707,54 @@ def run_cg(lq, ctx, torch, maxiter=20000):
     return res
 
 
+def run_multi_rhs_cg(lq, ctx, torch):
+    """24^4 Haar, m = 0.05, 8 right-hand sides, FP32-12 inner, tol 1e-10: one multi-RHS
+    solve on the paired layout, the same solve on the canonical layout, and the 8 systems
+    solved one at a time."""
+    import synth
+    dims, mass, nrhs = (24, 24, 24, 24), 0.05, 8
+    U = torch.from_numpy(synth.gauge_field(dims, "haar", seed=6)).cuda()
+    b = torch.from_numpy(synth.fermion_field(dims, nrhs, seed=7)).cuda()
+    x = torch.empty_like(b)
+    hi = lq.lq_gauge_pack(ctx, dims, U, "f64", 18)
+    lo = lq.lq_gauge_pack(ctx, dims, U, "f32", 12)
+    res = {"workload": "24^4 Haar SU(3), m=0.05, 8 Gaussian sources, FP32 inner (12-real), tol 1e-10 "
+                       "(FP64 true residual)"}
+    prev = os.environ.get("LQCD_CG_PAIRED")
+
+    def solve(bb, xx, n):
+        try:  # a short solve first: tunes the launch shapes outside the timed solve
+            lq.cg_solve(ctx, hi, lo, mass, bb, xx, n, tol=1e-10, maxiter=200)
+        except lq.LQError:
+            pass
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = lq.cg_solve(ctx, hi, lo, mass, bb, xx, n, tol=1e-10, maxiter=20000)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st
+
+    try:
+        for name, flag in (("paired", "1"), ("canonical", "0")):
+            os.environ["LQCD_CG_PAIRED"] = flag
+            dt, st = solve(b, x, nrhs)
+            it = max(s_["iters"] for s_ in st)
+            res[name] = {"seconds": round(dt, 4), "iters": it, "us_per_iter": round(1e6 * dt / it, 1),
+                         "max_true_rel_resid": max(s_["true_rel_resid"] for s_ in st)}
+        total = 0.0
+        for k in range(nrhs):
+            dt, _ = solve(b[k:k + 1].contiguous(), x[k:k + 1], 1)
+            total += dt
+        res["one_at_a_time_seconds"] = round(total, 4)
+        res["speedup_paired_vs_one_at_a_time"] = round(total / res["paired"]["seconds"], 2)
+        res["speedup_paired_vs_canonical"] = round(res["canonical"]["seconds"] / res["paired"]["seconds"], 3)
+    finally:
+        if prev is None:
+            os.environ.pop("LQCD_CG_PAIRED", None)
+        else:
+            os.environ["LQCD_CG_PAIRED"] = prev
+    return res
+
+
 def run_batched(lq, ctx, torch):
     """Lattices 8^4, 12^4, 16^4, 24^4, 8 Gaussian right-hand sides each, links exp(i 0.2 H),
     m = 0.1, FP32 inner iteration (12-real links), tol 1e-8: one batched solve against the
@@ -875,6 +923,7 @@ def run_ours(args):
         extra["cg"] = run_cg(lq, ctx, torch, args.cg_maxiter)
         if not args.no_batched_force:
             extra["batched"] = run_batched(lq, ctx, torch)
+            extra["multi_rhs_cg"] = run_multi_rhs_cg(lq, ctx, torch)
             extra["force"] = run_force(lq, ctx, torch)
     line = {
         "metric": METRIC,
