@@ -125,7 +125,28 @@ __global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const 
   using T = typename C::real;
   using V = typename C::vec;
   const int rhs = blockIdx.y;
+  const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
+  V* xc = reinterpret_cast<V*>(x) + rhs * nch;
+  V* rc = reinterpret_cast<V*>(r) + rhs * nch;
+  const V* pc = reinterpret_cast<const V*>(p) + rhs * nch;
+  const V* ac = reinterpret_cast<const V*>(Ap) + rhs * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  V xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
+  auto load = [&](size_t b0) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = b0 + u * stride;
+      if (i < nch) {
+        xw[u] = xc[i];
+        rw[u] = rc[i];
+        pw[u] = __ldg(pc + i);
+        aw[u] = __ldg(ac + i);
+      }
+    }
+  };
   pdl_wait();
+  load(i0);   // the thread's first chunks are in flight while alpha is formed
   CGScalars* sc = reinterpret_cast<CGScalars*>(red.finisher_state) + rhs;
   // alpha = rr / <p,Ap> from the kPapGroups group sums (block 0 records it in the state;
   // the FIN_BETA finisher at the end reads none of these fields)
@@ -147,24 +168,7 @@ __global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const 
   const T alpha = (T)s_alpha;
   double acc[1] = {0.0};
   float ks = 0.f, kc = 0.f;   // FP32: compensated running sum (Kahan) and its correction
-  const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
-  V* xc = reinterpret_cast<V*>(x) + rhs * nch;
-  V* rc = reinterpret_cast<V*>(r) + rhs * nch;
-  const V* pc = reinterpret_cast<const V*>(p) + rhs * nch;
-  const V* ac = reinterpret_cast<const V*>(Ap) + rhs * nch;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
-    V xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const size_t i = i0 + u * stride;
-      if (i < nch) {
-        xw[u] = xc[i];
-        rw[u] = rc[i];
-        pw[u] = __ldg(pc + i);
-        aw[u] = __ldg(ac + i);
-      }
-    }
+  for (; i0 < nch; i0 += kUnroll * stride) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const size_t i = i0 + u * stride;
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const 
       xc[i] = C::put(xv);
       rc[i] = C::put(rv);
     }
+    if (i0 + kUnroll * stride < nch) load(i0 + kUnroll * stride);
   }
   pdl_trigger();
   if constexpr (VP == LQ_F64) {
@@ -213,24 +218,28 @@ __global__ void __launch_bounds__(kBlas, 4) k_cg_xpay(const void* r, void* p, co
   using T = typename C::real;
   using V = typename C::vec;
   const int rhs = blockIdx.y;
+  const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
+  const V* rc = reinterpret_cast<const V*>(r) + rhs * nch;
+  V* pc = reinterpret_cast<V*>(p) + rhs * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  constexpr int kU = VP == LQ_F64 ? 2 : kUnroll;   // (FP64: four would spill)
+  size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  V rw[kU], pw[kU];
+  auto load = [&](size_t b0) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const size_t i = b0 + u * stride;
+      if (i < nch) {
+        rw[u] = __ldg(rc + i);
+        pw[u] = pc[i];
+      }
+    }
+  };
   pdl_wait();
+  load(i0);   // in flight while the scalars are read (wasted only for an inactive rhs)
   if (sc[rhs].active) {
     const T beta = (T)sc[rhs].beta;
-    const size_t nch = (size_t)Vh * VecT<VP>::bytes_per_site / 16;
-    const V* rc = reinterpret_cast<const V*>(r) + rhs * nch;
-    V* pc = reinterpret_cast<V*>(p) + rhs * nch;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    constexpr int kU = VP == LQ_F64 ? 2 : kUnroll;   // (FP64: four would spill)
-    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kU * stride) {
-      V rw[kU], pw[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const size_t i = i0 + u * stride;
-        if (i < nch) {
-          rw[u] = __ldg(rc + i);
-          pw[u] = pc[i];
-        }
-      }
+    for (; i0 < nch; i0 += kU * stride) {
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const size_t i = i0 + u * stride;
@@ -242,6 +251,7 @@ __global__ void __launch_bounds__(kBlas, 4) k_cg_xpay(const void* r, void* p, co
         for (int k = 0; k < C::n; ++k) pv[k] = fma(beta, pv[k], rv[k]);
         pc[i] = C::put(pv);
       }
+      if (i0 + kU * stride < nch) load(i0 + kU * stride);
     }
   }
   pdl_trigger();
@@ -338,24 +348,28 @@ __global__ void __launch_bounds__(kBlas) k_fold(double* x_hi, void* x_lo, int Vh
 __global__ void __launch_bounds__(kBlas, 4) k_cgp_xpay(const float4* r, float4* p, const CGScalars* sc, int Vh,
                                                        int nrhs) {
   const int pr = blockIdx.y, ra = 2 * pr, rb = 2 * pr + 1;
+  const size_t nch = (size_t)3 * Vh;
+  const float4* rc = r + pr * nch;
+  float4* pc = p + pr * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float4 rw[kUnroll], pw[kUnroll];
+  auto load = [&](size_t b0) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = b0 + u * stride;
+      if (i < nch) {
+        rw[u] = __ldg(rc + i);
+        pw[u] = pc[i];
+      }
+    }
+  };
   pdl_wait();
+  load(i0);   // in flight while the scalars are read
   const bool actA = sc[ra].active != 0, actB = rb < nrhs && sc[rb].active != 0;
   if (actA || actB) {
     const float bA = actA ? (float)sc[ra].beta : 0.f, bB = actB ? (float)sc[rb].beta : 0.f;
-    const size_t nch = (size_t)3 * Vh;
-    const float4* rc = r + pr * nch;
-    float4* pc = p + pr * nch;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
-      float4 rw[kUnroll], pw[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const size_t i = i0 + u * stride;
-        if (i < nch) {
-          rw[u] = __ldg(rc + i);
-          pw[u] = pc[i];
-        }
-      }
+    for (; i0 < nch; i0 += kUnroll * stride) {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         const size_t i = i0 + u * stride;
@@ -371,6 +385,7 @@ __global__ void __launch_bounds__(kBlas, 4) k_cgp_xpay(const float4* r, float4* 
         }
         pc[i] = q;
       }
+      if (i0 + kUnroll * stride < nch) load(i0 + kUnroll * stride);
     }
   }
   pdl_trigger();
@@ -381,7 +396,28 @@ __global__ void __launch_bounds__(kBlas, 4) k_cgp_xpay(const float4* r, float4* 
 __global__ void __launch_bounds__(kBlas, 2) k_cgp_update(float4* x, float4* r, const float4* p, const float4* Ap,
                                                          const double* gsum, int Vh, int nrhs, Reducer red) {
   const int pr = blockIdx.y;
+  const size_t nch = (size_t)3 * Vh;
+  float4* xc = x + pr * nch;
+  float4* rc = r + pr * nch;
+  const float4* pc = p + pr * nch;
+  const float4* ac = Ap + pr * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float4 xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
+  auto load = [&](size_t b0) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const size_t i = b0 + u * stride;
+      if (i < nch) {
+        xw[u] = xc[i];
+        rw[u] = rc[i];
+        pw[u] = __ldg(pc + i);
+        aw[u] = __ldg(ac + i);
+      }
+    }
+  };
   pdl_wait();
+  load(i0);   // in flight while alpha is formed
   CGScalars* sc = reinterpret_cast<CGScalars*>(red.finisher_state);
   __shared__ double s_alpha[2];
   if (threadIdx.x < 64) {   // warp 0: rhs 2 pr, warp 1: rhs 2 pr + 1
@@ -411,24 +447,7 @@ __global__ void __launch_bounds__(kBlas, 2) k_cgp_update(float4* x, float4* r, c
     c_ = (t - s_) - y;
     s_ = t;
   };
-  const size_t nch = (size_t)3 * Vh;
-  float4* xc = x + pr * nch;
-  float4* rc = r + pr * nch;
-  const float4* pc = p + pr * nch;
-  const float4* ac = Ap + pr * nch;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nch; i0 += kUnroll * stride) {
-    float4 xw[kUnroll], rw[kUnroll], pw[kUnroll], aw[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const size_t i = i0 + u * stride;
-      if (i < nch) {
-        xw[u] = xc[i];
-        rw[u] = rc[i];
-        pw[u] = __ldg(pc + i);
-        aw[u] = __ldg(ac + i);
-      }
-    }
+  for (; i0 < nch; i0 += kUnroll * stride) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const size_t i = i0 + u * stride;
@@ -443,6 +462,7 @@ __global__ void __launch_bounds__(kBlas, 2) k_cgp_update(float4* x, float4* r, c
       xc[i] = xv;
       rc[i] = rv;
     }
+    if (i0 + kUnroll * stride < nch) load(i0 + kUnroll * stride);
   }
   pdl_trigger();
   const float acc[2] = {sA - cA, sB - cB};
