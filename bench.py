@@ -374,6 +374,21 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
     peak, _ = measured_peak()
     Vh = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) // 2
     if want("formats"):
+        # the error each storage format costs: one half Dslash of the ring's input against the
+        # library's FP64 operator (FP64 links and vectors, pinned to the oracle at 1e-13 by the
+        # tests) applied to the unrounded input
+        chi64 = torch.from_numpy(synth.fermion_field(DIMS, 1, seed=2)).cuda()
+        g64 = lq.lq_gauge_pack(ctx, DIMS, U_dev, "f64", 18)
+        ref64 = torch.empty_like(chi64)
+        lq.dslash_eo(ctx, g64, chi64, ref64, 1, 1, lq.LQ_F64)
+        torch.cuda.synchronize()
+        del g64
+
+        def as_c128(t):
+            if t.is_complex():
+                return t.to(torch.complex128)
+            return torch.view_as_complex(t.float().contiguous()).to(torch.complex128)
+
         for prec, recon, vec in forms:
             sb = site_bytes(prec, recon, vec)
             K = ring_size(Vh * sb, l2, nstreams)
@@ -384,9 +399,13 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             del g
             us = ms * 1000.0 / launches
             gbs = Vh * sb / us / 1e3
+            lq.dslash_eo(ctx, gauges[0], ins[0], ts[0], 1, 1, vc)
+            torch.cuda.synchronize()
+            err = float(torch.linalg.vector_norm(as_c128(ts[0]) - ref64) / torch.linalg.vector_norm(ref64))
             out[f"{prec}/{recon}/{vec}"] = {"gflops": round(Vh * FLOPS_PER_SITE / us / 1e3, 1),
                                            "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
-                                           "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K}
+                                           "us_per_half": round(us, 2), "bytes_per_site": sb, "ring": K,
+                                           "rel_err_vs_fp64": float("%.3g" % err)}
             del gauges, ins, ts, outs
             torch.cuda.empty_cache()
     if want("l2_warm"):
