@@ -394,7 +394,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             K = ring_size(Vh * sb, l2, nstreams)
             gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, prec, recon, vec, K)
             vc = lq.PREC[vec]
-            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, APPS), nstreams)
             ms, launches, _ = time_steps(torch, g, 10, 3, stream)
             del g
             us = ms * 1000.0 / launches
@@ -415,7 +415,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
         gauges, ins, ts, outs = make_ring(lq, ctx, U_dev, DIMS, "f32", 18, "f32", 1)
         K = 2 * nstreams
         gauges, ins, ts, outs = gauges * K, ins * K, [ts[0]] * K, [outs[0]] * K
-        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, 20), nstreams)
+        g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, lq.PREC["f32"], ss, APPS), nstreams)
         ms, launches, _ = time_steps(torch, g, 10, 3, stream)
         del g
         us = ms * 1000.0 / launches
@@ -435,7 +435,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             K = ring_size(Vh4 * sb, l2, nstreams)
             gauges, ins, ts, outs = make_ring(lq, ctx, U4, d4, prec, recon, vec, K)
             vc = lq.PREC[vec]
-            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, 20), nstreams)
+            g = GraphStep(torch, lambda ss: run_step(lq, ctx, gauges, ins, ts, outs, vc, ss, APPS), nstreams)
             ms, launches, _ = time_steps(torch, g, 5, 3, stream)
             del g
             us = ms * 1000.0 / launches
@@ -463,7 +463,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             K = ring_size(Vhl * sb, l2, 1)
             gauges, ins, ts, outs = make_ring(lq, lctx, Ul, dims, prec, recon, vec, K)
             vc = lq.PREC[vec]
-            g = GraphStep(torch, lambda ss: run_step(lq, lctx, gauges, ins, ts, outs, vc, ss, 20), 1)
+            g = GraphStep(torch, lambda ss: run_step(lq, lctx, gauges, ins, ts, outs, vc, ss, APPS), 1)
             ms, launches, _ = time_steps(torch, g, 10, 3, stream)
             del g
             us = ms * 1000.0 / launches
@@ -493,13 +493,13 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
 
             def istep(ss, fats=fats, lngs=lngs, ins=ins, vc=vc):
                 h = 0
-                for a in range(20):
+                for a in range(APPS):
                     s_ = ss[a % len(ss)]
                     c, c2 = h % K, (h + 1) % K
                     lq.dslash_eo_improved(ctx, fats[c], lngs[c], ins[c], itmp[a % len(ss)], 1, 1, vc, s_)
                     lq.dslash_eo_improved(ctx, fats[c2], lngs[c2], itmp[a % len(ss)], iout[a % len(ss)], 0, 1, vc, s_)
                     h += 2
-                return 40
+                return 2 * APPS
             itmp = [torch.empty_like(ins[0]) for _ in range(nstreams)]
             iout = [torch.empty_like(ins[0]) for _ in range(nstreams)]
             g = GraphStep(torch, istep, nstreams)
@@ -528,13 +528,13 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
 
             def wstep(ss, wg=wg, wins=wins, wtmp=wtmp, wout=wout, vc=vc, K=K):
                 h = 0
-                for a in range(20):
+                for a in range(APPS):
                     s_ = ss[a % len(ss)]
                     c, c2 = h % K, (h + 1) % K
                     lq.dslash_wilson_eo(ctx, wg[c], wins[c], wtmp[a % len(ss)], 1, 1, vc, 1, s_)
                     lq.dslash_wilson_eo(ctx, wg[c2], wtmp[a % len(ss)], wout[a % len(ss)], 0, 1, vc, 1, s_)
                     h += 2
-                return 40
+                return 2 * APPS
             g = GraphStep(torch, wstep, nstreams)
             ms, launches, _ = time_steps(torch, g, 10, 3, stream)
             del g
@@ -568,7 +568,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
 
                 def mstep(ss, gauges=gauges, ins=ins, ts=ts, outs=outs, nrhs=nrhs, layout=layout):
                     h = 0
-                    for a in range(10):
+                    for a in range(APPS):
                         s_ = ss[a % len(ss)]
                         c, c2 = h % K, (h + 1) % K
                         if layout == "paired":
@@ -578,7 +578,7 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
                             lq.dslash_eo(ctx, gauges[c], ins[c], ts[c], 1, nrhs, lq.LQ_F32, s_)
                             lq.dslash_eo(ctx, gauges[c2], ts[c], outs[c], 0, nrhs, lq.LQ_F32, s_)
                         h += 2
-                    return 20
+                    return 2 * APPS
                 g = GraphStep(torch, mstep, nstreams)
                 ms, launches, _ = time_steps(torch, g, 10, 3, stream)
                 del g
@@ -606,9 +606,9 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             cs = [torch.empty_like(bs[0]) for _ in range(K)]
             for adj in (0, 1):
                 def step(ss):
-                    for i in range(20):
+                    for i in range(2 * APPS):
                         lq.su3_matvec_batch(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, None, ss[i % len(ss)])
-                    return 20
+                    return 2 * APPS
                 g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
@@ -636,10 +636,10 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             cs = [torch.empty_like(bs[0]) for _ in range(K)]
             for adj in (0, 1):
                 def step(ss, As=As, bs=bs, cs=cs, mat=mat, recon=recon, vec=vec, adj=adj):
-                    for i in range(20):
+                    for i in range(2 * APPS):
                         lq.su3_matvec_batch_ex(ctx, As[i % K], bs[i % K], cs[i % K], n, adj, mat, recon, vec,
                                                ss[i % len(ss)])
-                    return 20
+                    return 2 * APPS
                 g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
@@ -660,9 +660,9 @@ def run_variants(lq, ctx, torch, U_dev, l2, stream, nstreams, groups="all", fp64
             Cs = [torch.empty_like(As[0]) for _ in range(K)]
             for adjA, adjB in ((0, 0), (1, 0), (0, 1)):
                 def step(ss):
-                    for i in range(20):
+                    for i in range(2 * APPS):
                         lq.su3_mul_batch(ctx, As[i % K], Bs[i % K], Cs[i % K], n, adjA, adjB, None, ss[i % len(ss)])
-                    return 20
+                    return 2 * APPS
                 g = GraphStep(torch, step, nstreams)
                 ms, launches, _ = time_steps(torch, g, 5, 2, stream)
                 del g
