@@ -198,9 +198,18 @@ def make_ring(lq, ctx, U_dev, dims, prec, recon, vec, K, seed=2, nrhs=1):
             return torch.view_as_real(src).to(dt).contiguous().cuda()
         return torch.empty((nrhs, Vh, 3, 2), dtype=dt, device="cuda")
 
-    ins = [vec_tensor(host) for _ in range(K)]
-    ts = [vec_tensor() for _ in range(K)]
-    outs = [vec_tensor() for _ in range(K)]
+    def ring_of(src=None):
+        # the K copies as views of one contiguous tensor (a step's inputs or outputs move
+        # between host and device as one copy)
+        one = vec_tensor(src)
+        whole = torch.empty((K,) + tuple(one.shape), dtype=one.dtype, device="cuda")
+        if src is not None:
+            whole.copy_(one.unsqueeze(0).expand_as(whole))
+        return [whole[k] for k in range(K)]
+
+    ins = ring_of(host)
+    ts = ring_of()
+    outs = ring_of()
     return gauges, ins, ts, outs
 
 
@@ -893,35 +902,44 @@ def run_ours(args):
     # memory, issues every half-Dslash as its own dslash_eo call through the binding and the C
     # ABI (no graph: argument checks, tuning-table lookup and launch run per call), and copies
     # the outputs back.
-    host_in = [torch.empty_like(t, device="cpu").pin_memory() for t in ins]
-    for h, t in zip(host_in, ins):
-        h.copy_(t)
-    host_out = [torch.empty_like(t, device="cpu").pin_memory() for t in outs]
+    # the ring's K input copies are views of one contiguous tensor (make_ring): one
+    # pinned-host copy in and one out per step, the same bytes as K separate copies
+    def whole(views):
+        base = views[0]
+        n = len(views)
+        assert all(v.data_ptr() == base.data_ptr() + k * base.numel() * base.element_size()
+                   for k, v in enumerate(views))
+        return base.as_strided((n,) + tuple(base.shape), (base.numel(),) + tuple(base.stride()))
+
+    dev_in, dev_out = whole(ins), whole(outs)
+    host_in = [torch.empty_like(dev_in, device="cpu").pin_memory()]
+    host_in[0].copy_(dev_in)
+    host_out = [torch.empty_like(dev_out, device="cpu").pin_memory()]
+    ins_all, outs_all = [dev_in], [dev_out]
     side = [stream] + [torch.cuda.Stream() for _ in range(args.streams - 1)]
 
     def e2e_step():
-        for h, t in zip(host_in, ins):
+        for h, t in zip(host_in, ins_all):
             t.copy_(h, non_blocking=True)
         for s_ in side[1:]:
             s_.wait_stream(stream)
         n = run_step(lq, ctx, gauges, ins, ts, outs, vc, side, nrhs=nrhs)
         for s_ in side[1:]:
             stream.wait_stream(s_)
-        for h, t in zip(host_out, outs):
+        for h, t in zip(host_out, outs_all):
             h.copy_(t, non_blocking=True)
         return n
 
     e2e_steps = max(1, args.steps // 2)
     ms_e2e, _, _ = time_steps(torch, e2e_step, e2e_steps, min(args.warmup, 3), stream, dist, device)
     e2e_val = e2e_steps * APPS * 2 * Vh * nrhs * FLOPS_PER_SITE * world / (ms_e2e * 1e-3) / 1e9
-    vbytes = ins[0].numel() * ins[0].element_size()
 
     # the same with the step's launches replayed from a CUDA graph (copies still every step)
     def e2e_graph_step():
-        for h, t in zip(host_in, ins):
+        for h, t in zip(host_in, ins_all):
             t.copy_(h, non_blocking=True)
         n = step()
-        for h, t in zip(host_out, outs):
+        for h, t in zip(host_out, outs_all):
             h.copy_(t, non_blocking=True)
         return n
 
@@ -970,8 +988,9 @@ def run_ours(args):
                      "kernel": "k_dslash", "bytes_per_launch": Vh * sb,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                      "us_per_launch": round(us_per_launch, 3)},
-        "e2e": {"value": round(e2e_val, 1), "unit": "GFLOP/s", "h2d_bytes_per_step": K * vbytes,
-                "d2h_bytes_per_step": K * vbytes,
+        "e2e": {"value": round(e2e_val, 1), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in ins_all),
+                "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in outs_all),
                 "path": f"pinned host -> device copies, {2 * APPS} dslash_eo calls through the binding and "
                         f"the C ABI on {args.streams} streams, device -> pinned host copies, every step",
                 "graph_replay_value": round(e2e_graph_val, 1)},
