@@ -125,9 +125,11 @@ def test_cg_multi_rhs_paired_layout(lq, monkeypatch, lo, recon, nrhs, shape):
                 continue
             assert st[k]["true_rel_resid"] <= 1e-10
             assert _true_resid(U, b[k], xs[layout][k], mass, dims) <= 1.05e-10
+    # both solutions meet a 1e-10 true residual: they agree to within cond(M) * 2e-10
+    # (cond(M) ~ 400 here), far below anything a layout error would give
     for k in range(nrhs):
         if k != nrhs // 2:
-            assert rel_l2(xs["1"][k], xs["0"][k]) < 1e-8
+            assert rel_l2(xs["1"][k], xs["0"][k]) < 1e-7
 
 
 def test_cg_zero_source_and_failures(lq, ctx):
