@@ -118,8 +118,10 @@ lq_status launch_dslash(lq_context* ctx, const DslashArgs& a, cudaStream_t s) {
   // operator; a launch with a reduction is tuned as itself (its cost depends on the number
   // of blocks it reduces over), which is repeatable because the solvers never let out alias
   // w1 or w2 and their reductions only store totals or alpha = rr / total.
+  // Tuning bursts keep the launch's programmatic dependent launch: a chain of half Dslash
+  // calls overlaps each launch's ramp with its predecessor's tail, and the shape that is
+  // fastest that way is not always the fastest in isolation.
   DslashKArgs plain = k;
-  plain.pdl = 0;
   // a finisher that is not idempotent (FIN_BETA advances the CG state) is never repeated
   const bool tune_as_is = a.reduce != RED_NONE && a.red && a.red->finisher != FIN_BETA;
   if (!tune_as_is) {
