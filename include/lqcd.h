@@ -108,7 +108,10 @@ lq_status lq_selftest_wait_timeout(lq_context* ctx, lq_stream stream);
  * launch's own parallelism matters less than its instruction count.  Tuning must not
  * happen during stream capture: make one uncaptured call with the same shapes first.  The
  * environment variable LQCD_DSLASH_SHAPE="block,rhs_tile,threads_per_site" forces one
- * shape for every Dslash launch it fits (block 64..256, a multiple of 32). */
+ * shape for every Dslash launch it fits (block 64..256, a multiple of 32).  threads_per_site
+ * 1, 2 or 4 selects the split-site kernel; 8 the rhs-per-warp multi-RHS kernel (rhs_tile =
+ * right-hand sides per block); 16 the link-staging kernel (rhs_tile 1); 32 the paired-layout
+ * kernel of dslash_eo_paired (rhs_tile = pairs of right-hand sides per thread: 1, 2, 4). */
 lq_status lq_set_tuning(lq_context* ctx, int mode);
 /* Persist the tuning table in the file `path` (NULL or "" stops persisting): the entries
  * the file holds for this device (same name and SM count) are loaded now, without
