@@ -34,6 +34,7 @@
 #include "dslash_multi.cuh"
 #include "dslash_paired.cuh"
 #include "lqcd_internal.cuh"
+#include "tma.cuh"
 #include "tune.cuh"
 
 bool dslash_vec_ok(lq_prec gauge, lq_prec vec);
@@ -207,6 +208,117 @@ __global__ void __launch_bounds__(kBlas, 2) k_cg_update(void* x, void* r, const 
     const float accf[1] = {ks - kc};   // the thread's sum, then the compensated warp tree
     block_reduce<1>(accf, red, rhs, gridDim.y);
   }
+}
+
+// The FP32 update of k_cg_update with its operands streamed through shared memory by TMA
+// bulk copies: one block per SM, tiles of kUpdTile 16-byte chunks of x, r, p and Ap (64 KB)
+// in a ring of kUpdStages stages.  Thread 0 issues the four copies of a tile kUpdStages - 1
+// tiles ahead and waits for the current one on its mbarrier (bounded: on time-out it sets
+// kDevTmaTimeout in *status, waits once more for every copy it issued and the block stops);
+// the threads read the tile from shared memory and store x and r to global memory.  Two
+// tiles (128 KB per SM) are always in flight, without registers holding them.
+constexpr int kUpdTile = 1024;
+constexpr int kUpdStages = 3;
+constexpr size_t kUpdSmem = (size_t)kUpdStages * 4 * kUpdTile * sizeof(float4);
+__global__ void __launch_bounds__(kBlas, 1) k_cg_update_tma(float4* x, float4* r, const float4* p, const float4* Ap,
+                                                            const double* gsum, int Vh, Reducer red,
+                                                            unsigned int* status) {
+  extern __shared__ __align__(128) unsigned char upd_raw[];
+  float4* stg = reinterpret_cast<float4*>(upd_raw);   // [stage][x, r, p, Ap][kUpdTile]
+  __shared__ uint64_t bar[kUpdStages];
+  __shared__ int ok_s;
+  __shared__ double s_alpha;
+  const int rhs = blockIdx.y;
+  const size_t nch = (size_t)Vh * 3 / 2;              // 24 bytes per site, 16 per chunk
+  float4* xc = x + rhs * nch;
+  float4* rc = r + rhs * nch;
+  const float4* pc = p + rhs * nch;
+  const float4* ac = Ap + rhs * nch;
+  const size_t ntile = (nch + kUpdTile - 1) / kUpdTile;
+  const int nmine = blockIdx.x < ntile ? (int)((ntile - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kUpdStages; ++k) tma::mbar_init(&bar[k], 1);
+  }
+  __syncthreads();
+  pdl_wait();
+  auto tile_of = [&](int k, size_t& c0, uint32_t& n) {
+    c0 = ((size_t)blockIdx.x + (size_t)k * gridDim.x) * kUpdTile;
+    n = (uint32_t)(nch - c0 < (size_t)kUpdTile ? nch - c0 : (size_t)kUpdTile);
+  };
+  auto issue = [&](int k) {   // thread 0: tile k of this block into stage k % kUpdStages
+    size_t c0;
+    uint32_t n;
+    tile_of(k, c0, n);
+    uint64_t* b = &bar[k % kUpdStages];
+    float4* sg = stg + (size_t)(k % kUpdStages) * 4 * kUpdTile;
+    tma::mbar_expect_tx(b, 4 * n * (uint32_t)sizeof(float4));
+    tma::load(sg, xc + c0, n * sizeof(float4), b);
+    tma::load(sg + kUpdTile, rc + c0, n * sizeof(float4), b);
+    tma::load(sg + 2 * kUpdTile, pc + c0, n * sizeof(float4), b);
+    tma::load(sg + 3 * kUpdTile, ac + c0, n * sizeof(float4), b);
+  };
+  int issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < kUpdStages - 1 && issued < nmine; ++issued) issue(issued);
+  CGScalars* sc = reinterpret_cast<CGScalars*>(red.finisher_state) + rhs;
+  if (threadIdx.x < 32) {   // alpha = rr / <p,Ap> from the kPapGroups group sums
+    double v = __ldcg(gsum + (size_t)rhs * kPapGroups + threadIdx.x);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) {
+      const double a = (sc->active && v > 0.0) ? sc->rr / v : 0.0;
+      s_alpha = a;
+      if (blockIdx.x == 0) {
+        sc->pAp = v;
+        sc->alpha = a;
+        if (sc->active) sc->alpha_last = a;
+      }
+    }
+  }
+  __syncthreads();
+  const float alpha = (float)s_alpha;
+  float ks = 0.f, kc = 0.f;
+  for (int k = 0; k < nmine; ++k) {
+    if (threadIdx.x == 0) {
+      if (issued < nmine) issue(issued++);   // into the stage freed at the end of tile k - 1
+      int ok = tma::mbar_wait(&bar[k % kUpdStages], (k / kUpdStages) & 1) ? 1 : 0;
+      if (!ok) {
+        atomicOr(status, kDevTmaTimeout);
+        for (int j = k; j < issued; ++j) tma::mbar_wait(&bar[j % kUpdStages], (j / kUpdStages) & 1);
+      }
+      ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) break;   // copies that did not arrive: the block stops (the solve reports it)
+    size_t c0;
+    uint32_t n;
+    tile_of(k, c0, n);
+    const float4* sg = stg + (size_t)(k % kUpdStages) * 4 * kUpdTile;
+#pragma unroll
+    for (int j = 0; j < kUpdTile / kBlas; ++j) {
+      const uint32_t i = threadIdx.x + j * kBlas;
+      if (i >= n) break;
+      float4 xv = sg[i], rv = sg[kUpdTile + i];
+      const float4 pv = sg[2 * kUpdTile + i], av = sg[3 * kUpdTile + i];
+      xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
+      xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
+      rv.x = fmaf(-alpha, av.x, rv.x); rv.y = fmaf(-alpha, av.y, rv.y);
+      rv.z = fmaf(-alpha, av.z, rv.z); rv.w = fmaf(-alpha, av.w, rv.w);
+      const float q[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float y = fmaf(q[m], q[m], -kc);
+        const float t = ks + y;
+        kc = (t - ks) - y;
+        ks = t;
+      }
+      xc[c0 + i] = xv;
+      rc[c0 + i] = rv;
+    }
+    __syncthreads();   // stage k % kUpdStages is free again
+  }
+  pdl_trigger();
+  const float accf[1] = {ks - kc};
+  block_reduce<1>(accf, red, rhs, gridDim.y);
 }
 
 // p = r + beta p for active right-hand sides.  grid = (nbx, nrhs), about one wave of
@@ -804,9 +916,22 @@ lq_status launch_blas_update(Solver& S) {
   }
   // about two blocks per SM over all right-hand sides: fewer block reductions (FP64), each
   // thread streaming more chunks
+  Reducer red = S.reducer(FIN_BETA);
+  if (S.vp == LQ_F32 && S.nrhs == 1) {
+    // one block per SM, operands through shared memory by TMA.  Measured at 32^4: 104.2
+    // against 105.2 us per FP32-12 iteration; with 8 right-hand sides (19 blocks each) the
+    // register-staged kernel below is faster (162.9 against 164.4 us at 24^4).
+    LQ_CUDA(S.ctx, cudaFuncSetAttribute(k_cg_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kUpdSmem));
+    const int nt = std::max(1, (S.ctx->num_sms + S.nrhs - 1) / S.nrhs);
+    cudaError_t e = launch_k(k_cg_update_tma, dim3(nt, S.nrhs), dim3(kBlas), kUpdSmem, S.s, S.pdl, (float4*)S.xl,
+                             (float4*)S.r, (const float4*)S.p, (const float4*)S.Ap, (const double*)S.gsum, S.Vh, red,
+                             S.ctx->dev_status);
+    if (e != cudaSuccess) return lq_cuda_fail(S.ctx, e, "k_cg_update_tma");
+    return LQ_OK;
+  }
   const int nb = std::min(S.nbx, std::max(1, (2 * S.ctx->num_sms + S.nrhs - 1) / S.nrhs));
   dim3 grid(nb, S.nrhs);
-  Reducer red = S.reducer(FIN_BETA);
   cudaError_t e = S.vp == LQ_F64
                       ? launch_k(k_cg_update<LQ_F64>, grid, dim3(kBlas), 0, S.s, S.pdl, S.xl, S.r, (const void*)S.p,
                                  (const void*)S.Ap, (const double*)S.gsum, S.Vh, red)
