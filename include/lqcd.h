@@ -77,8 +77,9 @@ const char* lq_last_error(const lq_context* ctx);
 const char* lq_status_string(lq_status s);
 /* Synchronise `stream`, then report and clear the context's device status word: the
  * flags that bounded device waits set when they gave up since the last lq_sync.  Such a
- * wait exists in the batched SU(3) kernels (su3_*_batch) and in the link-staging half
- * Dslash (dslash_eo and the solvers, when the tuner picks it), where one thread per block
+ * wait exists in the batched SU(3) kernels (su3_*_batch), in the link-staging half
+ * Dslash (dslash_eo and the solvers, when the tuner picks it) and in the single-RHS FP32
+ * update of the mixed CG (cg_solve, cg_solve_noalloc), where one thread per block
  * waits, at most ~2^24 polls, for the TMA bulk copies that bring the block's operand slices
  * into shared memory; if they do not arrive, the block records the failure, waits once
  * more (bounded) so that it does not leave with copies in flight, and skips its work.
